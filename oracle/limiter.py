@@ -1,0 +1,118 @@
+"""TVB-minmod limiter on 2D Cartesian meshes, applied in characteristic fields.
+
+The paper applies "the standard TVB minmod limiters" of Cockburn and Shu's
+RKDG paper on multidimensional systems (Sec. 4.2), once per cRKDG step at the
+final stage (Remark 2.2), with parameter M (M = 50 for the double Mach
+reflection, Sec. 4.2.2).  The paper does not print the limiter; the reading
+implemented here (parity unpinned against the paper; pinned by invariants):
+
+  per direction (x shown; y alike with mode (0,1), dy, N/S neighbours):
+    a1 = u_(1,0)                (the xi-slope coefficient of the cell)
+    a2 = ubar_E - ubar_K,  a3 = ubar_K - ubar_W
+  for systems, project onto characteristic fields with L_x(ubar_K) = R_x^{-1},
+  R_x the right eigenvectors of d f_x / d u at the cell average;
+  modified minmod, per field:
+    mt = a1                     if |a1| <= M dx^2
+    mt = minmod(a1, a2, a3)     otherwise   (minmod = s min|.| if all signs
+                                              equal s, else 0)
+  the cell is troubled if mt != a1 in any field of x or y.  A troubled cell
+  keeps its average, gets u_(1,0) = R_x mt_x, u_(0,1) = R_y mt_y, and all
+  other modes are set to zero.
+
+Ghost averages across a boundary: periodic -> neighbour across the domain;
+outflow -> own average; reflect -> own average with the normal momentum
+negated; ('dirichlet', g) -> g at the ghost-cell centre and time t;
+('custom', h) -> h(own average, ghost-cell centre, t).
+Test infrastructure only.
+"""
+import numpy as np
+
+from .physics import Euler
+
+
+def minmod3(a, b, c):
+    s = np.sign(a)
+    same = (np.sign(b) == s) & (np.sign(c) == s)
+    m = np.minimum(np.minimum(np.abs(a), np.abs(b)), np.abs(c))
+    return np.where(same, s * m, 0.0)
+
+
+def tvb_minmod(a1, a2, a3, Mh2):
+    return np.where(np.abs(a1) <= Mh2, a1, minmod3(a1, a2, a3))
+
+
+def ghost_average(dg, side, avg, t):
+    """Average of the ghost cell beyond a non-periodic side, from the own
+    averages of the boundary cells avg (n, nv)."""
+    bc = dg.bc[side]
+    axis = 0 if side in ("E", "W") else 1
+    if bc == "outflow":
+        return avg.copy()
+    if bc == "reflect":
+        out = avg.copy()
+        out[:, 1 + axis] = -out[:, 1 + axis]
+        return out
+    if side in ("E", "W"):
+        X = np.full(dg.ny, dg.x1 + 0.5 * dg.dx if side == "E" else dg.x0 - 0.5 * dg.dx)
+        Y = dg.yc
+    else:
+        X = dg.xc
+        Y = np.full(dg.nx, dg.y1 + 0.5 * dg.dy if side == "N" else dg.y0 - 0.5 * dg.dy)
+    kind, fn = bc
+    if kind == "dirichlet":
+        return np.asarray(fn(X, Y, t), dtype=np.float64) + 0 * avg
+    return np.asarray(fn(avg, X, Y, t), dtype=np.float64)
+
+
+def neighbour_averages(dg, avg, t):
+    nb = {"E": np.roll(avg, -1, axis=1), "W": np.roll(avg, 1, axis=1),
+          "N": np.roll(avg, -1, axis=0), "S": np.roll(avg, 1, axis=0)}
+    if dg.bc["E"] != "periodic":
+        nb["E"][:, -1] = ghost_average(dg, "E", avg[:, -1], t)
+        nb["W"][:, 0] = ghost_average(dg, "W", avg[:, 0], t)
+    if dg.bc["N"] != "periodic":
+        nb["N"][-1, :] = ghost_average(dg, "N", avg[-1, :], t)
+        nb["S"][0, :] = ghost_average(dg, "S", avg[0, :], t)
+    return nb
+
+
+def tvb_limit(dg, u, M, t):
+    """Return (limited copy of u, boolean troubled-cell map)."""
+    u = np.array(u, dtype=np.float64, copy=True)
+    if dg.B.nm < 3:
+        return u, np.zeros((dg.ny, dg.nx), dtype=bool)
+    avg = u[..., 0]
+    nb = neighbour_averages(dg, avg, t)
+    systems = isinstance(dg.phys, Euler)
+    flags = np.zeros((dg.ny, dg.nx), dtype=bool)
+    newx = np.empty_like(u[..., 1])
+    newy = np.empty_like(u[..., 2])
+    for y in range(dg.ny):
+        for x in range(dg.nx):
+            ab = avg[y, x]
+            ax = (u[y, x, :, 1], nb["E"][y, x] - ab, ab - nb["W"][y, x])
+            ay = (u[y, x, :, 2], nb["N"][y, x] - ab, ab - nb["S"][y, x])
+            if systems:
+                Rx = dg.phys.right_eigenvectors(ab, 0)
+                Ry = dg.phys.right_eigenvectors(ab, 1)
+                Lx, Ly = np.linalg.inv(Rx), np.linalg.inv(Ry)
+                cx = [Lx @ a for a in ax]
+                cy = [Ly @ a for a in ay]
+            else:
+                cx, cy = list(ax), list(ay)
+            mx = tvb_minmod(cx[0], cx[1], cx[2], M * dg.dx * dg.dx)
+            my = tvb_minmod(cy[0], cy[1], cy[2], M * dg.dy * dg.dy)
+            flags[y, x] = bool(np.any(mx != cx[0]) or np.any(my != cy[0]))
+            newx[y, x] = Rx @ mx if systems else mx
+            newy[y, x] = Ry @ my if systems else my
+    out = u.copy()
+    f = flags
+    out[f, :, 1] = newx[f]
+    out[f, :, 2] = newy[f]
+    out[f, :, 3:] = 0.0
+    return out, flags
+
+
+def make_limiter(dg, M):
+    """limiter(u, t) -> limited u, for use with the step functions."""
+    return lambda u, t: tvb_limit(dg, u, M, t)[0]

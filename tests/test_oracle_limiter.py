@@ -1,0 +1,111 @@
+"""Pins of the oracle's TVB-minmod limiter (reading of Sec. 4.2; the paper
+does not print the limiter, so these are invariants, not printed values)."""
+import numpy as np
+import pytest
+
+import crkdg_inputs as inp
+from oracle import tableaux as TB
+from oracle.dg2d import DG2D, crkdg_step
+from oracle.limiter import make_limiter, minmod3, tvb_limit
+from oracle.physics import Advection, Euler
+
+PER = {s: "periodic" for s in "WESN"}
+OUT = {s: "outflow" for s in "WESN"}
+
+
+def test_minmod_closed_forms():
+    assert minmod3(np.array(1.0), np.array(2.0), np.array(3.0)) == 1.0
+    assert minmod3(np.array(-3.0), np.array(-2.0), np.array(-5.0)) == -2.0
+    assert minmod3(np.array(1.0), np.array(-2.0), np.array(3.0)) == 0.0
+    assert minmod3(np.array(0.0), np.array(1.0), np.array(1.0)) == 0.0
+
+
+def test_eigenvectors_diagonalise_the_jacobian():
+    """R diag(lambda) R^{-1} equals the flux Jacobian, obtained here by
+    central differences of the flux."""
+    ph = Euler(1.4, 2)
+    u = inp.conserved(1.3, 0.4, -0.7, 2.1)
+    for axis in (0, 1):
+        R = ph.right_eigenvectors(u, axis)
+        rho, vel, p = ph.primitive(u)
+        c = np.sqrt(1.4 * p / rho)
+        vn = vel[axis]
+        lam = np.diag([vn - c, vn, vn, vn + c])
+        J = np.empty((4, 4))
+        for j in range(4):
+            e = np.zeros(4)
+            e[j] = 1e-6
+            J[:, j] = (ph.flux(u + e, axis) - ph.flux(u - e, axis)) / 2e-6
+        assert np.allclose(R @ lam @ np.linalg.inv(R), J, atol=1e-7)
+
+
+def _euler_dg(n=10, bc=PER, k=2):
+    return DG2D(n, n, (0, 1, 0, 1), k, "P", Euler(1.4, 2), bc)
+
+
+def test_averages_are_preserved_and_high_modes_cleared():
+    dg = _euler_dg()
+    u = inp.random_modal_state(10, 10, 2, "P", "euler", seed=11, amp=0.8)
+    v, flags = tvb_limit(dg, u, 0.0, 0.0)
+    assert flags.any()
+    assert np.array_equal(v[..., 0], u[..., 0])
+    assert np.all(v[flags][..., 3:] == 0)
+    assert np.array_equal(v[~flags], u[~flags])
+
+
+def test_smooth_data_with_large_M_is_untouched():
+    dg = _euler_dg()
+    u = inp.random_modal_state(10, 10, 2, "P", "euler", seed=12)
+    v, flags = tvb_limit(dg, u, 1e8, 0.0)
+    assert not flags.any()
+    assert np.array_equal(u, v)
+
+
+def test_linear_data_is_not_flagged():
+    """A linear function: a1 equals both neighbour differences (in scalar and
+    in characteristic fields alike), so minmod returns a1."""
+    dg = DG2D(8, 8, (0, 1, 0, 1), 2, "P", Advection([1.0, 1.0]), OUT)
+    u = dg.project(lambda X, Y: (2 * X - 3 * Y)[..., None])
+    # the outflow ghost copies the cell itself: drop the boundary ring
+    v, flags = tvb_limit(dg, u, 0.0, 0.0)
+    assert not flags[1:-1, 1:-1].any()
+
+
+def test_step_profile_flags_only_cells_at_the_jump():
+    dg = _euler_dg(n=12, bc=OUT)
+    u = dg.project(lambda X, Y: np.where((X < 0.52)[..., None], inp.conserved(1.0, 0, 0, 1.0),
+                                         inp.conserved(0.125, 0, 0, 0.1)))
+    # M h^2 > 0 keeps roundoff-level slopes of the constant cells unflagged
+    v, flags = tvb_limit(dg, u, 1.0, 0.0)
+    # the jump sits inside column 6; its neighbours are constant (a1 = 0)
+    assert flags[:, 6].all()
+    assert not flags[:, :6].any() and not flags[:, 7:].any()
+
+
+def test_limiter_is_idempotent_on_its_output():
+    dg = _euler_dg()
+    u = inp.random_modal_state(10, 10, 2, "P", "euler", seed=13, amp=0.8)
+    v, _ = tvb_limit(dg, u, 10.0, 0.0)
+    w, _ = tvb_limit(dg, v, 10.0, 0.0)
+    assert np.max(np.abs(w - v)) < 1e-12
+
+
+def test_conservation_with_limiter():
+    dg = _euler_dg(n=8)
+    u = inp.random_modal_state(8, 8, 2, "P", "euler", seed=14, amp=0.2)
+    lim = make_limiter(dg, 1.0)
+    m0 = dg.total(u)
+    for _ in range(5):
+        u = crkdg_step(dg, u, 0.0, 0.002, TB.SSPRK3, limiter=lim)
+    assert np.all(np.abs(dg.total(u) - m0) <= 1e-13 * np.abs(m0))
+
+
+def test_reflective_ghost_negates_normal_momentum():
+    from oracle.limiter import neighbour_averages
+    bc = {"W": "reflect", "E": "reflect", "S": "reflect", "N": "reflect"}
+    dg = _euler_dg(n=4, bc=bc)
+    u = inp.random_modal_state(4, 4, 2, "P", "euler", seed=15)
+    nb = neighbour_averages(dg, u[..., 0], 0.0)
+    a = u[..., 0]
+    assert np.allclose(nb["W"][:, 0, 1], -a[:, 0, 1]) and np.allclose(nb["W"][:, 0, 2], a[:, 0, 2])
+    assert np.allclose(nb["N"][-1, :, 2], -a[-1, :, 2]) and np.allclose(nb["N"][-1, :, 1], a[-1, :, 1])
