@@ -1,0 +1,197 @@
+/*
+ * crkdg.h -- C ABI of the GB300 (sm_103a) compact RKDG time step.
+ *
+ * The library advances hyperbolic conservation laws u_t + div f(u) = 0 with
+ * the compact Runge--Kutta discontinuous Galerkin (cRKDG) method of Chen, Sun
+ * and Xing (arXiv 2307.06471), on uniform Cartesian meshes in 1D and 2D:
+ *   inner stages (eq. (2.8), first line):
+ *       u^(i) = u^n - dt sum_{j<i} a_ij div^loc f(u^(j))
+ *     with the cell-local operator of eq. (2.7) (no neighbour data);
+ *   final stage (eq. (2.8), second line):
+ *       u^{n+1} = u^n - dt sum_i b_i div^DG f(u^(i))
+ *     with the DG operator of eq. (2.3) and the Lax--Friedrichs flux of
+ *     Sec. 2.1 (alpha local to each face point and stage);
+ *   a TVB-minmod limiter applied once per step, after the final stage
+ *     (Remark 2.2; Sec. 4.2).
+ *
+ * Conventions (all calls):
+ *   - every call returns a crkdg_status; nothing throws across the ABI;
+ *     crkdg_last_error() gives a thread-local message for the last failure;
+ *   - host arrays are owned by the caller and only read/written during the
+ *     call; device memory is owned by the context;
+ *   - calls run asynchronously on the context's CUDA stream unless marked
+ *     "synchronises";
+ *   - device-side failures (non-physical states, NaN, bounded waits that ran
+ *     out) are recorded in a device status word read by crkdg_sync(); no
+ *     kernel traps.
+ *
+ * State layout (host and device): planes [v][m][y][x], x fastest, with
+ *   v   the conserved variable (advection: u; 1D Euler: rho, rho w, E;
+ *       2D Euler: rho, rho w, rho v, E),
+ *   m   the Legendre mode on the reference cell [-1,1]^d:
+ *       1D: P_m(xi), m = 0..k;
+ *       2D: P_i(xi) P_j(eta) ordered by total degree i + j ascending and,
+ *       within one degree, by i descending; P^k takes i + j <= k, Q^k takes
+ *       i, j <= k (so P^k is a prefix of Q^k and modes 0, 1, 2 are
+ *       (0,0), (1,0), (0,1)).  Mode 0 is the cell average.
+ *   1D meshes use ny = 1.
+ */
+#ifndef CRKDG_H
+#define CRKDG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRKDG_MAX_STAGES 6
+
+typedef enum {
+    CRKDG_OK = 0,
+    CRKDG_EINVAL = -1,         /* bad argument (message in crkdg_last_error) */
+    CRKDG_ENOMEM = -2,         /* device or host allocation failed */
+    CRKDG_ECUDA = -3,          /* a CUDA runtime call failed */
+    CRKDG_ENONPHYSICAL = -4,   /* device saw rho <= 0, p <= 0 or NaN */
+    CRKDG_ETIMEOUT = -5,       /* a bounded device wait ran out */
+    CRKDG_EUNSUPPORTED = -6    /* combination not built (e.g. k > 3) */
+} crkdg_status;
+
+/* device status bits returned by crkdg_sync */
+#define CRKDG_ST_NONPHYSICAL 0x1u
+#define CRKDG_ST_NAN 0x2u
+#define CRKDG_ST_TIMEOUT 0x4u
+
+/* boundary condition of one side */
+enum { CRKDG_BC_PERIODIC = 0, CRKDG_BC_OUTFLOW = 1, CRKDG_BC_REFLECT = 2, CRKDG_BC_DIRICHLET = 3 };
+/* built-in exterior data for CRKDG_BC_DIRICHLET sides (bc_params per side):
+ *   CONST       params[0..nv-1] = exterior state
+ *   SINE        advection: A sin(kx x + ky y - w t + phi); params A, kx, ky, w, phi
+ *   SINE_PROD   advection: A sin(kx (x - cx t)) sin(ky (y - cy t)); params A, kx, cx, ky, cy
+ *   DMR_BOTTOM  x < x0: post-shock state, else reflecting wall; params post[4], x0
+ *   DMR_TOP     x < x0 + s_y y + s_t t: post-shock, else pre-shock;
+ *               params post[4], pre[4], x0, s_y, s_t
+ * Exterior data for stage i are evaluated at t^n + c_i dt (Sec. 2.1, 3.4). */
+enum { CRKDG_FN_CONST = 0, CRKDG_FN_SINE = 1, CRKDG_FN_SINE_PROD = 2, CRKDG_FN_DMR_BOTTOM = 3,
+       CRKDG_FN_DMR_TOP = 4 };
+
+enum { CRKDG_SIDE_W = 0, CRKDG_SIDE_E = 1, CRKDG_SIDE_S = 2, CRKDG_SIDE_N = 3 };
+enum { CRKDG_ADVECTION = 0, CRKDG_EULER = 1 };
+enum { CRKDG_BASIS_P = 0, CRKDG_BASIS_Q = 1 };
+enum { CRKDG_F32 = 0, CRKDG_F64 = 1 };
+enum { CRKDG_FLUX_LLF = 0 };   /* Lax--Friedrichs, alpha per face point and stage */
+
+typedef struct {
+    int dim;                   /* 1 or 2 */
+    int nx, ny;                /* cells; ny = 1 when dim = 1 */
+    double x0, x1, y0, y1;     /* domain [x0,x1] x [y0,y1] */
+    int bc[4];                 /* CRKDG_BC_* for W, E, S, N (periodic pairs) */
+    int bc_fn[4];              /* CRKDG_FN_* for Dirichlet sides */
+    double bc_params[4][16];   /* per-side parameters of bc_fn */
+} crkdg_mesh;
+
+/* Butcher tableau of eq. (2.5): a strictly lower triangular, row-major s x s
+ * in a[CRKDG_MAX_STAGES * CRKDG_MAX_STAGES] (row i at a[i*CRKDG_MAX_STAGES]),
+ * weights b[s], nodes c[s]. */
+typedef struct {
+    int s;
+    double a[CRKDG_MAX_STAGES * CRKDG_MAX_STAGES];
+    double b[CRKDG_MAX_STAGES];
+    double c[CRKDG_MAX_STAGES];
+} crkdg_tableau;
+
+typedef struct crkdg_ctx crkdg_ctx;   /* opaque; owns all device buffers */
+
+/* Create a solver context (eq. (2.1) on `mesh`, space P^k/Q^k, Sec. 2.1).
+ *   k          polynomial degree 0..3
+ *   basis      CRKDG_BASIS_P or _Q (ignored in 1D)
+ *   flux       CRKDG_FLUX_LLF
+ *   tab        explicit Butcher tableau, 1 <= s <= CRKDG_MAX_STAGES
+ *   gamma      ratio of specific heats (Euler)
+ *   physics    CRKDG_ADVECTION (phys_params = beta_x, beta_y) or CRKDG_EULER
+ *   precision  CRKDG_F32 (bulk FP32, FP64 reductions) or CRKDG_F64
+ *   stream     cudaStream_t to run on (NULL: the legacy default stream)
+ * Allocates the state (two ping-pong copies) and scratch on the current
+ * device.  Returns CRKDG_EINVAL / CRKDG_EUNSUPPORTED / CRKDG_ENOMEM. */
+int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab,
+                 double gamma, int physics, int precision, const double* phys_params,
+                 void* stream, crkdg_ctx** out);
+void crkdg_destroy(crkdg_ctx* ctx);
+
+/* Sizes: cells = nx*ny, modes per cell, variables, volume points per cell. */
+int crkdg_sizes(const crkdg_ctx* ctx, int* n_cells, int* n_modes, int* n_vars, int* n_qp);
+
+/* Coordinates of the volume quadrature points (tensor Gauss--Legendre, k+1
+ * per direction), host array xy[cell][q][dim], cell = y*nx + x.  Pure host
+ * computation. */
+int crkdg_quadrature_points(const crkdg_ctx* ctx, double* xy);
+
+/* L2 projection (Sec. 2.2, the Pi of eq. (2.7)) of point values of the
+ * initial data, values[cell][q][v] (FP64, host), by the volume Gauss rule;
+ * replaces the state, sets t = 0 and clears any pending limit.  Synchronises. */
+int crkdg_project_ic(crkdg_ctx* ctx, const double* values);
+
+/* Replace / read the state, host FP64 planes [v][m][y][x].  get_state first
+ * applies a pending limit (see crkdg_limit).  Both synchronise. */
+int crkdg_set_state(crkdg_ctx* ctx, const double* host_state, double t);
+int crkdg_get_state(crkdg_ctx* ctx, double* host_state);
+
+/* FP64 CFL time step dt = cfl / max_K (s_x(ubar)/dx + s_y(ubar)/dy) over cell
+ * averages (1D: cfl * dx / max |f'|).  Synchronises. */
+int crkdg_cfl_dt(crkdg_ctx* ctx, double cfl, double* dt_out);
+
+/* One full cRKDG step of size dt (eq. (2.8)), asynchronous: all inner
+ * stages, the final DG stage with boundary data at t^n + c_i dt, the limiter
+ * of a previous step (applied on load) and the FP64 reductions of the new
+ * cell averages (max wave speed, totals).  t advances by dt. */
+int crkdg_step(crkdg_ctx* ctx, double dt);
+
+/* March n_steps steps with dt computed on the device from the previous
+ * step's FP64 wave-speed reduction, dt = min(cfl/maxspeed, t_end - t); no
+ * host synchronisation between steps.  Steps whose dt would be <= 0 copy the
+ * state.  With capture != 0 the n_steps launches are recorded once into a
+ * CUDA graph and replayed on later calls with the same n_steps. */
+int crkdg_advance(crkdg_ctx* ctx, int n_steps, double cfl, double t_end, int capture);
+
+/* Limiter control (Remark 2.2).  M >= 0: enable the TVB-minmod limiter with
+ * parameter M for the end of every following step, and mark the current
+ * state as pending a limit (it is limited before its next use: on load by
+ * the next step, or by get_state).  M < 0: disable for following steps (a
+ * pending limit of an earlier step is still applied). */
+int crkdg_limit(crkdg_ctx* ctx, double M_tvb);
+
+/* Fixed-dt run of n_steps steps.  1D meshes of up to 960 cells run the whole
+ * sequence in one single-block launch (block barrier between steps). */
+int crkdg_run_fixed(crkdg_ctx* ctx, int n_steps, double dt);
+
+/* Totals sum_K |K| ubar_K per variable (FP64, eq. (3.4)).  Synchronises. */
+int crkdg_conservation(crkdg_ctx* ctx, double* sums);
+
+/* Number of cells the limiter flagged as troubled in the last limited step
+ * (counted on the device).  Synchronises. */
+int crkdg_troubled_count(crkdg_ctx* ctx, unsigned long long* count);
+
+/* Wait for the stream; return the device status bits seen so far (and
+ * clear them).  Returns CRKDG_ENONPHYSICAL if any bit is set. */
+int crkdg_sync(crkdg_ctx* ctx, unsigned* device_status);
+
+/* Current simulation time (host copy). */
+int crkdg_time(const crkdg_ctx* ctx, double* t);
+
+/* Launch shape of the fused 2D step: rows per warp segment and warps per
+ * block (0 = keep).  crkdg_autotune times candidates on the current state
+ * (state restored afterwards) and keeps the fastest; returns its time/step
+ * in microseconds. */
+int crkdg_set_launch(crkdg_ctx* ctx, int seg_rows, int warps_per_block);
+int crkdg_get_launch(const crkdg_ctx* ctx, int* seg_rows, int* warps_per_block);
+int crkdg_autotune(crkdg_ctx* ctx, double* best_us);
+
+/* Checkpoint: header + FP64 state; load restores state, t and limiter. */
+int crkdg_save(crkdg_ctx* ctx, const char* path);
+int crkdg_load(crkdg_ctx* ctx, const char* path);
+
+const char* crkdg_last_error(void);
+const char* crkdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRKDG_H */

@@ -1,0 +1,237 @@
+"""ctypes binding of the cRKDG C ABI (include/crkdg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The functions below carry the ABI's names; ``Solver`` is a thin
+object wrapper around one context.  Importing this module does not load the
+library; the first call does, and raises if libcrkdg.so is missing -- there
+is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcrkdg.so")
+MAX_STAGES = 6
+
+OK, EINVAL, ENOMEM, ECUDA, ENONPHYSICAL, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_DIRICHLET = 0, 1, 2, 3
+FN_CONST, FN_SINE, FN_SINE_PROD, FN_DMR_BOTTOM, FN_DMR_TOP = 0, 1, 2, 3, 4
+ADVECTION, EULER = 0, 1
+BASIS_P, BASIS_Q = 0, 1
+F32, F64 = 0, 1
+FLUX_LLF = 0
+ST_NONPHYSICAL, ST_NAN, ST_TIMEOUT = 1, 2, 4
+
+
+class CrkdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("crkdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("bc", C.c_int * 4), ("bc_fn", C.c_int * 4), ("bc_params", (C.c_double * 16) * 4)]
+
+
+class Tableau(C.Structure):
+    _fields_ = [("s", C.c_int), ("a", C.c_double * (MAX_STAGES * MAX_STAGES)),
+                ("b", C.c_double * MAX_STAGES), ("c", C.c_double * MAX_STAGES)]
+
+
+_lib = None
+
+_SIGS = {
+    "crkdg_create": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.POINTER(Tableau), C.c_double,
+                               C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "crkdg_destroy": (None, [C.c_void_p]),
+    "crkdg_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 4),
+    "crkdg_quadrature_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_project_ic": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_set_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double]),
+    "crkdg_get_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_cfl_dt": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "crkdg_step": (C.c_int, [C.c_void_p, C.c_double]),
+    "crkdg_advance": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
+    "crkdg_run_fixed": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "crkdg_limit": (C.c_int, [C.c_void_p, C.c_double]),
+    "crkdg_conservation": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_troubled_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
+    "crkdg_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint)]),
+    "crkdg_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "crkdg_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "crkdg_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "crkdg_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "crkdg_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "crkdg_last_error": (C.c_char_p, []),
+    "crkdg_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libcrkdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcrkdg.so not built: run paper_2307_06471_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != OK:
+        raise CrkdgError(code, lib().crkdg_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_tableau(A, b):
+    t = Tableau()
+    s = len(b)
+    t.s = s
+    for i in range(s):
+        t.b[i] = b[i]
+        t.c[i] = sum(A[i][:i])
+        for j in range(s):
+            t.a[i * MAX_STAGES + j] = A[i][j]
+    return t
+
+
+def make_mesh(dim, nx, ny, box, bc, bc_fn=(0, 0, 0, 0), bc_params=None):
+    m = Mesh()
+    m.dim, m.nx, m.ny = dim, nx, ny
+    m.x0, m.x1 = box[0], box[1]
+    m.y0, m.y1 = (box[2], box[3]) if dim == 2 else (0.0, 1.0)
+    for s in range(4):
+        m.bc[s] = bc[s]
+        m.bc_fn[s] = bc_fn[s]
+        if bc_params is not None and bc_params[s] is not None:
+            for j, v in enumerate(bc_params[s]):
+                m.bc_params[s][j] = float(v)
+    return m
+
+
+class Solver:
+    """One cRKDG context.  State arrays are FP64 numpy planes [v, m, y, x]."""
+
+    def __init__(self, mesh, k, basis, tableau, physics, precision, gamma=1.4, beta=(1.0, 0.0), stream=None):
+        L = lib()
+        self.ctx = C.c_void_p()
+        pp = np.asarray(beta, dtype=np.float64)
+        self._pp = pp
+        tab = make_tableau(*tableau) if not isinstance(tableau, Tableau) else tableau
+        _check(L.crkdg_create(C.byref(mesh), k, basis, FLUX_LLF, C.byref(tab), gamma, physics, precision,
+                              _dptr(pp), C.c_void_p(stream) if stream else None, C.byref(self.ctx)))
+        self.mesh = mesh
+        nc, nm, nv, nq = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(L.crkdg_sizes(self.ctx, C.byref(nc), C.byref(nm), C.byref(nv), C.byref(nq)))
+        self.n_cells, self.n_modes, self.n_vars, self.n_qp = nc.value, nm.value, nv.value, nq.value
+        self.shape = (self.n_vars, self.n_modes, mesh.ny if mesh.dim == 2 else 1, mesh.nx)
+
+    def close(self):
+        if self.ctx:
+            lib().crkdg_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def quadrature_points(self):
+        dim = self.mesh.dim
+        xy = np.empty(self.n_cells * self.n_qp * dim)
+        _check(lib().crkdg_quadrature_points(self.ctx, _dptr(xy)))
+        return xy.reshape(self.n_cells, self.n_qp, dim)
+
+    def project_ic(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float64).reshape(self.n_cells, self.n_qp, self.n_vars)
+        _check(lib().crkdg_project_ic(self.ctx, _dptr(v)))
+
+    def project_function(self, fn):
+        """fn(X[, Y]) -> (..., nv) evaluated at the quadrature points."""
+        xy = self.quadrature_points()
+        if self.mesh.dim == 1:
+            vals = fn(xy[..., 0])
+        else:
+            vals = fn(xy[..., 0], xy[..., 1])
+        self.project_ic(np.asarray(vals, dtype=np.float64).reshape(self.n_cells, self.n_qp, self.n_vars))
+
+    def set_state(self, u, t=0.0):
+        a = np.ascontiguousarray(u, dtype=np.float64)
+        assert a.size == np.prod(self.shape)
+        _check(lib().crkdg_set_state(self.ctx, _dptr(a), float(t)))
+
+    def get_state(self):
+        a = np.empty(self.shape)
+        _check(lib().crkdg_get_state(self.ctx, _dptr(a)))
+        return a
+
+    def cfl_dt(self, cfl):
+        d = C.c_double()
+        _check(lib().crkdg_cfl_dt(self.ctx, cfl, C.byref(d)))
+        return d.value
+
+    def step(self, dt):
+        _check(lib().crkdg_step(self.ctx, float(dt)))
+
+    def advance(self, n_steps, cfl, t_end, capture=False):
+        _check(lib().crkdg_advance(self.ctx, int(n_steps), float(cfl), float(t_end), 1 if capture else 0))
+
+    def run_fixed(self, n_steps, dt):
+        _check(lib().crkdg_run_fixed(self.ctx, int(n_steps), float(dt)))
+
+    def limit(self, M):
+        _check(lib().crkdg_limit(self.ctx, float(M)))
+
+    def conservation(self):
+        s = np.empty(self.n_vars)
+        _check(lib().crkdg_conservation(self.ctx, _dptr(s)))
+        return s
+
+    def troubled_count(self):
+        c = C.c_ulonglong()
+        _check(lib().crkdg_troubled_count(self.ctx, C.byref(c)))
+        return c.value
+
+    def sync(self):
+        st = C.c_uint()
+        code = lib().crkdg_sync(self.ctx, C.byref(st))
+        return code, st.value
+
+    def time(self):
+        t = C.c_double()
+        _check(lib().crkdg_time(self.ctx, C.byref(t)))
+        return t.value
+
+    def set_launch(self, seg_rows=0, warps_per_block=0):
+        _check(lib().crkdg_set_launch(self.ctx, int(seg_rows), int(warps_per_block)))
+
+    def get_launch(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().crkdg_get_launch(self.ctx, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def autotune(self):
+        us = C.c_double()
+        _check(lib().crkdg_autotune(self.ctx, C.byref(us)))
+        return us.value
+
+    def save(self, path):
+        _check(lib().crkdg_save(self.ctx, path.encode()))
+
+    def load(self, path):
+        _check(lib().crkdg_load(self.ctx, path.encode()))

@@ -1,0 +1,715 @@
+// C ABI of the cRKDG library (include/crkdg.h): context management, argument
+// checking, state transfer, and the enqueueing of the step, limiter,
+// reduction and projection kernels on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/crkdg.h"
+#include "launch.h"
+
+using crk::DevState;
+using crk::StepArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(CRKDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct GraphKey {
+    int n, start, lim_first, lim_rest;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(n, start, lim_first, lim_rest) < std::tie(o.n, o.start, o.lim_first, o.lim_rest);
+    }
+};
+
+}  // namespace
+
+struct crkdg_ctx {
+    crkdg_mesh mesh;
+    int dim, k, basis, flux, physics, precision;
+    double gamma, beta[2];
+    crkdg_tableau tab;
+    int nv, nm, nqv;
+    size_t ncell, elems;
+    size_t esize;
+    void* u[2];
+    int cur;
+    double* d_tab;
+    DevState* d_state;
+    double* d_partials;
+    size_t partials_cap;
+    unsigned long long* d_flags;
+    cudaStream_t stream;
+    double t;
+    bool t_known;
+    bool limiter_on;
+    double M;
+    bool pending;
+    double M_pending;
+    int seg_rows, wpb;
+    int kphys;   // kernel physics id
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+int n_modes(int dim, int k, int basis) {
+    if (dim == 1) return k + 1;
+    return basis == CRKDG_BASIS_P ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 1);
+}
+
+double dx_of(const crkdg_ctx* c) { return (c->mesh.x1 - c->mesh.x0) / c->mesh.nx; }
+double dy_of(const crkdg_ctx* c) { return c->dim == 1 ? 1.0 : (c->mesh.y1 - c->mesh.y0) / c->mesh.ny; }
+
+StepArgs base_args(const crkdg_ctx* c) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = c->mesh.nx;
+    a.ny = c->dim == 1 ? 1 : c->mesh.ny;
+    a.x0 = c->mesh.x0;
+    a.y0 = c->mesh.y0;
+    a.dx = dx_of(c);
+    a.dy = dy_of(c);
+    a.ds = c->d_state;
+    a.partials = c->d_partials;
+    a.s = c->tab.s;
+    a.tab = c->d_tab;
+    for (int s = 0; s < 4; ++s) {
+        a.bc[s].type = c->mesh.bc[s];
+        a.bc[s].fn = c->mesh.bc_fn[s];
+        for (int j = 0; j < 16; ++j) a.bc[s].p[j] = c->mesh.bc_params[s][j];
+    }
+    a.gamma = c->gamma;
+    a.beta[0] = c->beta[0];
+    a.beta[1] = c->beta[1];
+    return a;
+}
+
+// launch geometry of the 2D step
+void strips_segs(const crkdg_ctx* c, int seg_rows, int* ns, int* nseg) {
+    *ns = (c->mesh.nx + 29) / 30;
+    *nseg = (c->mesh.ny + seg_rows - 1) / seg_rows;
+}
+
+int ensure_partials(crkdg_ctx* c, size_t n) {
+    if (n <= c->partials_cap) return CRKDG_OK;
+    if (c->d_partials) cudaFree(c->d_partials);
+    c->d_partials = nullptr;
+    CK(cudaMalloc(&c->d_partials, n * sizeof(double)));
+    c->partials_cap = n;
+    return CRKDG_OK;
+}
+
+int max_wpb(crkdg_ctx* c) {
+    crk::KernelInfo ki;
+    CK(crk::info_step2d(c->kphys, c->precision, c->k, c->basis, c->tab.s, &ki));
+    int by_regs = std::max(1, ki.max_threads / 32);
+    int by_smem = std::max(1, (227 * 1024) / (ki.smem_per_thread * 32));
+    return std::min(8, std::min(by_regs, by_smem));
+}
+
+int default_launch(crkdg_ctx* c) {
+    if (c->dim != 2) return CRKDG_OK;
+    const int ns = (c->mesh.nx + 29) / 30;
+    // about 8 resident warps on each of the 152 SMs, segments of >= 8 rows
+    const long target = 152L * 8;
+    int L = (int)std::max(8L, ((long)ns * c->mesh.ny + target - 1) / target);
+    L = std::min(L, c->mesh.ny);
+    c->seg_rows = L;
+    int w = max_wpb(c);
+    if (w < 0) return w;
+    c->wpb = std::min(w, 4);
+    return CRKDG_OK;
+}
+
+int enqueue_reduce(crkdg_ctx* c, int set_dt) {
+    const int blocks = 4 * 152;
+    int r = ensure_partials(c, (size_t)blocks * 8 * 8);
+    if (r) return r;
+    CK(crk::launch_reduce(c->dim, c->kphys, c->precision, c->u[c->cur], c->mesh.nx, c->dim == 1 ? 1 : c->mesh.ny, c->nm,
+                          dx_of(c), dy_of(c), c->gamma, c->beta[0], c->beta[1], c->d_state, c->d_partials, blocks,
+                          set_dt, c->stream));
+    return CRKDG_OK;
+}
+
+int enqueue_limit(crkdg_ctx* c, double M) {
+    StepArgs a = base_args(c);
+    a.M = M;
+    a.t = c->t;
+    CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, c->u[c->cur], c->d_flags, c->stream));
+    return CRKDG_OK;
+}
+
+// enqueue one 2D/1D step from u[cur] into u[cur^1]
+int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) {
+    StepArgs a = base_args(c);
+    a.uin = c->u[c->cur];
+    a.uout = c->u[c->cur ^ 1];
+    a.t = c->t;
+    a.dt = dt;
+    a.dt_from_dev = dt_from_dev;
+    a.limit = limit;
+    a.M = M;
+    if (c->dim == 2) {
+        int ns, nseg;
+        strips_segs(c, c->seg_rows, &ns, &nseg);
+        a.seg_len = c->seg_rows;
+        a.n_strips = ns;
+        a.n_segs = nseg;
+        int r = ensure_partials(c, (size_t)ns * nseg * 8);
+        if (r) return r;
+        a.partials = c->d_partials;
+        CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+    } else {
+        const int warps = (c->mesh.nx + 29) / 30;
+        const int blocks = (warps + 7) / 8;
+        CK(crk::launch_step1d(c->kphys, c->precision, c->k, a, 1, blocks == 1 ? warps * 32 : 256, blocks, c->stream));
+    }
+    c->cur ^= 1;
+    return CRKDG_OK;
+}
+
+int check_ctx(const crkdg_ctx* c) { return c ? CRKDG_OK : fail(CRKDG_EINVAL, "null context"); }
+
+__global__ void set_run_params(DevState* ds, double cfl, double t_end) {
+    ds->cfl = cfl;
+    ds->t_end = t_end;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* crkdg_last_error(void) { return g_err.c_str(); }
+const char* crkdg_version(void) { return "crkdg-gb300 1.0 (sm_103a)"; }
+
+int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab, double gamma,
+                 int physics, int precision, const double* phys_params, void* stream, crkdg_ctx** out) {
+    if (!mesh || !tab || !out) return fail(CRKDG_EINVAL, "null argument");
+    *out = nullptr;
+    if (mesh->dim != 1 && mesh->dim != 2) return fail(CRKDG_EINVAL, "dim must be 1 or 2");
+    if (mesh->nx < 1 || (mesh->dim == 2 && mesh->ny < 1)) return fail(CRKDG_EINVAL, "mesh must have cells");
+    if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
+        return fail(CRKDG_EINVAL, "empty domain");
+    if ((long long)mesh->nx * (mesh->dim == 2 ? mesh->ny : 1) > (1LL << 30))
+        return fail(CRKDG_EINVAL, "mesh too large (more than 2^30 cells)");
+    if (k < 0 || k > 3) return fail(CRKDG_EUNSUPPORTED, "k must be 0..3");
+    if (basis != CRKDG_BASIS_P && basis != CRKDG_BASIS_Q) return fail(CRKDG_EINVAL, "basis must be P or Q");
+    if (flux != CRKDG_FLUX_LLF) return fail(CRKDG_EINVAL, "flux must be CRKDG_FLUX_LLF");
+    if (physics != CRKDG_ADVECTION && physics != CRKDG_EULER) return fail(CRKDG_EINVAL, "unknown physics");
+    if (precision != CRKDG_F32 && precision != CRKDG_F64) return fail(CRKDG_EINVAL, "unknown precision");
+    if (tab->s < 1 || tab->s > CRKDG_MAX_STAGES) return fail(CRKDG_EINVAL, "tableau stages must be 1..6");
+    for (int i = 0; i < tab->s; ++i)
+        for (int j = i; j < CRKDG_MAX_STAGES; ++j)
+            if (tab->a[i * CRKDG_MAX_STAGES + j] != 0.0)
+                return fail(CRKDG_EINVAL, "tableau must be explicit (a strictly lower triangular)");
+    if (physics == CRKDG_EULER && !(gamma > 1.0)) return fail(CRKDG_EINVAL, "gamma must exceed 1");
+    if (physics == CRKDG_ADVECTION && !phys_params) return fail(CRKDG_EINVAL, "advection needs beta");
+    const int ns = mesh->dim == 1 ? 2 : 4;
+    for (int s = 0; s < ns; ++s) {
+        const int b = mesh->bc[s];
+        if (b < 0 || b > 3) return fail(CRKDG_EINVAL, "unknown boundary condition");
+        if (b == CRKDG_BC_REFLECT && physics != CRKDG_EULER) return fail(CRKDG_EINVAL, "reflect needs Euler");
+        if (b == CRKDG_BC_DIRICHLET && (mesh->bc_fn[s] < 0 || mesh->bc_fn[s] > 4))
+            return fail(CRKDG_EINVAL, "unknown boundary function");
+    }
+    if ((mesh->bc[0] == CRKDG_BC_PERIODIC) != (mesh->bc[1] == CRKDG_BC_PERIODIC))
+        return fail(CRKDG_EINVAL, "periodic W/E must come in pairs");
+    if (mesh->dim == 2 && (mesh->bc[2] == CRKDG_BC_PERIODIC) != (mesh->bc[3] == CRKDG_BC_PERIODIC))
+        return fail(CRKDG_EINVAL, "periodic S/N must come in pairs");
+
+    crkdg_ctx* c = new crkdg_ctx();
+    c->mesh = *mesh;
+    if (mesh->dim == 1) {
+        c->mesh.ny = 1;
+        c->mesh.y0 = 0.0;
+        c->mesh.y1 = 1.0;
+        c->mesh.bc[2] = c->mesh.bc[3] = CRKDG_BC_PERIODIC;
+    }
+    c->dim = mesh->dim;
+    c->k = k;
+    c->basis = mesh->dim == 1 ? CRKDG_BASIS_P : basis;
+    c->flux = flux;
+    c->physics = physics;
+    c->precision = precision;
+    c->gamma = gamma;
+    c->beta[0] = phys_params && physics == CRKDG_ADVECTION ? phys_params[0] : 0.0;
+    c->beta[1] = phys_params && physics == CRKDG_ADVECTION && mesh->dim == 2 ? phys_params[1] : 0.0;
+    c->tab = *tab;
+    c->nv = physics == CRKDG_ADVECTION ? 1 : (mesh->dim == 1 ? 3 : 4);
+    c->nm = n_modes(mesh->dim, k, c->basis);
+    c->nqv = mesh->dim == 1 ? k + 1 : (k + 1) * (k + 1);
+    c->ncell = (size_t)c->mesh.nx * c->mesh.ny;
+    c->elems = c->ncell * c->nv * c->nm;
+    c->esize = precision == CRKDG_F32 ? 4 : 8;
+    c->kphys = physics == CRKDG_ADVECTION ? crk::PHYS_ADV : (mesh->dim == 1 ? crk::PHYS_EULER1D : crk::PHYS_EULER);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->t = 0.0;
+    c->t_known = true;
+    c->M = -1.0;
+    c->seg_rows = 8;
+    c->wpb = 4;
+    auto bail = [&](int code) {
+        crkdg_destroy(c);
+        return code;
+    };
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMalloc(&c->u[b], c->elems * c->esize) != cudaSuccess)
+            return bail(fail(CRKDG_ENOMEM, "cudaMalloc of the state failed"));
+        cudaMemsetAsync(c->u[b], 0, c->elems * c->esize, c->stream);
+    }
+    double htab[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
+    for (int i = 0; i < crk::MAXS * crk::MAXS; ++i) htab[i] = tab->a[i];
+    for (int i = 0; i < tab->s; ++i) {
+        htab[crk::MAXS * crk::MAXS + i] = tab->b[i];
+        htab[crk::MAXS * crk::MAXS + crk::MAXS + i] = tab->c[i];
+    }
+    if (cudaMalloc(&c->d_tab, sizeof(htab)) != cudaSuccess ||
+        cudaMalloc(&c->d_state, sizeof(DevState)) != cudaSuccess ||
+        cudaMalloc(&c->d_flags, sizeof(unsigned long long)) != cudaSuccess)
+        return bail(fail(CRKDG_ENOMEM, "cudaMalloc failed"));
+    if (cudaMemcpy(c->d_tab, htab, sizeof(htab), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(CRKDG_ECUDA, "copy of the tableau failed"));
+    DevState ds;
+    std::memset(&ds, 0, sizeof(ds));
+    if (cudaMemcpy(c->d_state, &ds, sizeof(ds), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_flags, 0, sizeof(unsigned long long)) != cudaSuccess)
+        return bail(fail(CRKDG_ECUDA, "initialisation of the device state failed"));
+    int r = ensure_partials(c, 4096);
+    if (r) return bail(r);
+    r = default_launch(c);
+    if (r) return bail(r);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(CRKDG_ECUDA, "stream sync failed"));
+    *out = c;
+    return CRKDG_OK;
+}
+
+void crkdg_destroy(crkdg_ctx* c) {
+    if (!c) return;
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (int b = 0; b < 2; ++b)
+        if (c->u[b]) cudaFree(c->u[b]);
+    if (c->d_tab) cudaFree(c->d_tab);
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_flags) cudaFree(c->d_flags);
+    delete c;
+}
+
+int crkdg_sizes(const crkdg_ctx* c, int* n_cells, int* n_modes_, int* n_vars, int* n_qp) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (n_cells) *n_cells = (int)c->ncell;
+    if (n_modes_) *n_modes_ = c->nm;
+    if (n_vars) *n_vars = c->nv;
+    if (n_qp) *n_qp = c->nqv;
+    return CRKDG_OK;
+}
+
+int crkdg_quadrature_points(const crkdg_ctx* c, double* xy) {
+    if (check_ctx(c) || !xy) return fail(CRKDG_EINVAL, "null argument");
+    const crk::GaussRule g = crk::gauss_rule(c->k + 1);
+    const double dx = dx_of(c), dy = dy_of(c);
+    const int nq = c->k + 1;
+    size_t o = 0;
+    for (int y = 0; y < c->mesh.ny; ++y)
+        for (int x = 0; x < c->mesh.nx; ++x) {
+            const double xc = c->mesh.x0 + (x + 0.5) * dx, yc = c->mesh.y0 + (y + 0.5) * dy;
+            if (c->dim == 1) {
+                for (int q = 0; q < nq; ++q) xy[o++] = xc + 0.5 * dx * g.x[q];
+            } else {
+                for (int a = 0; a < nq; ++a)
+                    for (int b = 0; b < nq; ++b) {
+                        xy[o++] = xc + 0.5 * dx * g.x[a];
+                        xy[o++] = yc + 0.5 * dy * g.x[b];
+                    }
+            }
+        }
+    return CRKDG_OK;
+}
+
+int crkdg_project_ic(crkdg_ctx* c, const double* values) {
+    if (check_ctx(c) || !values) return fail(CRKDG_EINVAL, "null argument");
+    const size_t n = c->ncell * c->nqv * c->nv;
+    double* d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) return fail(CRKDG_ENOMEM, "cudaMalloc failed");
+    cudaError_t e = cudaMemcpyAsync(d, values, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = crk::launch_project(c->dim, c->kphys, c->precision, c->k, c->basis, d, c->u[c->cur], (int)c->ncell,
+                                c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CRKDG_ECUDA, std::string("project_ic: ") + cudaGetErrorString(e));
+    c->t = 0.0;
+    c->t_known = true;
+    c->pending = false;
+    CK(cudaMemcpy(&c->d_state->t, &c->t, sizeof(double), cudaMemcpyHostToDevice));
+    return CRKDG_OK;
+}
+
+int crkdg_set_state(crkdg_ctx* c, const double* h, double t) {
+    if (check_ctx(c) || !h) return fail(CRKDG_EINVAL, "null argument");
+    if (c->precision == CRKDG_F64) {
+        CK(cudaMemcpyAsync(c->u[c->cur], h, c->elems * 8, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<float> f(c->elems);
+        for (size_t i = 0; i < c->elems; ++i) f[i] = (float)h[i];
+        CK(cudaMemcpyAsync(c->u[c->cur], f.data(), c->elems * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->t = t;
+    c->t_known = true;
+    c->pending = false;
+    CK(cudaMemcpyAsync(&c->d_state->t, &c->t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CRKDG_OK;
+}
+
+int crkdg_get_state(crkdg_ctx* c, double* h) {
+    if (check_ctx(c) || !h) return fail(CRKDG_EINVAL, "null argument");
+    if (c->pending && c->dim == 2) {
+        if (!c->t_known) {
+            CK(cudaMemcpyAsync(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            c->t_known = true;
+        }
+        int r = enqueue_limit(c, c->M_pending);
+        if (r) return r;
+        c->pending = false;
+    }
+    if (c->precision == CRKDG_F64) {
+        CK(cudaMemcpyAsync(h, c->u[c->cur], c->elems * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> f(c->elems);
+        CK(cudaMemcpyAsync(f.data(), c->u[c->cur], c->elems * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < c->elems; ++i) h[i] = f[i];
+    }
+    return CRKDG_OK;
+}
+
+int crkdg_cfl_dt(crkdg_ctx* c, double cfl, double* dt_out) {
+    if (check_ctx(c) || !dt_out) return fail(CRKDG_EINVAL, "null argument");
+    if (!(cfl > 0.0)) return fail(CRKDG_EINVAL, "cfl must be positive");
+    int r = enqueue_reduce(c, 0);
+    if (r) return r;
+    double ms = 0.0;
+    CK(cudaMemcpyAsync(&ms, &c->d_state->maxspeed, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!(ms > 0.0) || !std::isfinite(ms)) return fail(CRKDG_ENONPHYSICAL, "wave speed is zero or not finite");
+    *dt_out = cfl / ms;
+    return CRKDG_OK;
+}
+
+int crkdg_step(crkdg_ctx* c, double dt) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(CRKDG_EINVAL, "dt must be positive and finite");
+    if (!c->t_known) {
+        CK(cudaMemcpyAsync(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->t_known = true;
+    }
+    const int lim = c->pending && c->dim == 2;
+    int r = enqueue_step(c, dt, 0, lim, lim ? c->M_pending : 0.0);
+    if (r) return r;
+    c->t += dt;
+    c->pending = c->limiter_on && c->dim == 2;
+    c->M_pending = c->M;
+    return CRKDG_OK;
+}
+
+int crkdg_advance(crkdg_ctx* c, int n_steps, double cfl, double t_end, int capture) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "crkdg_advance is 2D only (use crkdg_run_fixed in 1D)");
+    if (n_steps < 0) return fail(CRKDG_EINVAL, "n_steps must be >= 0");
+    if (!(cfl > 0.0)) return fail(CRKDG_EINVAL, "cfl must be positive");
+    if (n_steps == 0) return CRKDG_OK;
+    // run parameters and the first dt from the current state
+    set_run_params<<<1, 1, 0, c->stream>>>(c->d_state, cfl, t_end);
+    CK(cudaGetLastError());
+    int r = enqueue_reduce(c, 1);
+    if (r) return r;
+    const int lim_first = c->pending ? 1 : 0;
+    const int lim_rest = c->limiter_on ? 1 : 0;
+    const double M_first = c->M_pending, M_rest = c->M;
+    int ns, nseg;
+    strips_segs(c, c->seg_rows, &ns, &nseg);
+    r = ensure_partials(c, (size_t)ns * nseg * 8);
+    if (r) return r;
+    auto enqueue_all = [&]() -> int {
+        for (int i = 0; i < n_steps; ++i) {
+            const int lim = i == 0 ? lim_first : lim_rest;
+            int rr = enqueue_step(c, 0.0, 1, lim, i == 0 ? M_first : M_rest);
+            if (rr) return rr;
+        }
+        return CRKDG_OK;
+    };
+    if (!capture) {
+        r = enqueue_all();
+        if (r) return r;
+    } else {
+        GraphKey key{n_steps, c->cur, lim_first, lim_rest};
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            if (c->stream == nullptr) return fail(CRKDG_EINVAL, "graph capture needs a non-default stream");
+            const int cur0 = c->cur;
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            r = enqueue_all();
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (r) return r;
+            if (e != cudaSuccess) return fail(CRKDG_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+            cudaGraphExec_t ge;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(CRKDG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+            it = c->graphs.emplace(key, ge).first;
+            c->cur = cur0;   // capture recorded but did not run the steps
+        }
+        CK(cudaGraphLaunch(it->second, c->stream));
+        if (n_steps % 2) c->cur ^= 1;
+    }
+    c->t_known = false;
+    c->pending = c->limiter_on;
+    c->M_pending = c->M;
+    return CRKDG_OK;
+}
+
+int crkdg_run_fixed(crkdg_ctx* c, int n_steps, double dt) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (n_steps < 0 || !(dt > 0.0)) return fail(CRKDG_EINVAL, "need n_steps >= 0 and dt > 0");
+    if (c->dim == 2) {
+        for (int i = 0; i < n_steps; ++i) {
+            int r = crkdg_step(c, dt);
+            if (r) return r;
+        }
+        return CRKDG_OK;
+    }
+    const int warps = (c->mesh.nx + 29) / 30;
+    if (warps > 32) {
+        for (int i = 0; i < n_steps; ++i) {
+            int r = crkdg_step(c, dt);
+            if (r) return r;
+        }
+        return CRKDG_OK;
+    }
+    // whole run in one single-block launch
+    if (n_steps == 0) return CRKDG_OK;
+    StepArgs a = base_args(c);
+    a.uin = c->u[c->cur];
+    a.uout = c->u[c->cur ^ 1];
+    a.t = c->t;
+    a.dt = dt;
+    CK(crk::launch_step1d(c->kphys, c->precision, c->k, a, n_steps, warps * 32, 1, c->stream));
+    if (n_steps % 2) c->cur ^= 1;
+    c->t += n_steps * dt;
+    return CRKDG_OK;
+}
+
+int crkdg_limit(crkdg_ctx* c, double M) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "the TVB limiter is built for 2D meshes");
+    if (M >= 0.0) {
+        c->limiter_on = true;
+        c->M = M;
+        c->pending = true;
+        c->M_pending = M;
+    } else {
+        c->limiter_on = false;
+        c->M = -1.0;
+    }
+    return CRKDG_OK;
+}
+
+int crkdg_conservation(crkdg_ctx* c, double* sums) {
+    if (check_ctx(c) || !sums) return fail(CRKDG_EINVAL, "null argument");
+    int r = enqueue_reduce(c, 0);
+    if (r) return r;
+    CK(cudaMemcpyAsync(sums, c->d_state->sums, c->nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CRKDG_OK;
+}
+
+int crkdg_troubled_count(crkdg_ctx* c, unsigned long long* count) {
+    if (check_ctx(c) || !count) return fail(CRKDG_EINVAL, "null argument");
+    double tr = 0.0;
+    CK(cudaMemcpyAsync(&tr, &c->d_state->troubled, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = (unsigned long long)tr;
+    return CRKDG_OK;
+}
+
+int crkdg_sync(crkdg_ctx* c, unsigned* device_status) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, &c->d_state->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(&c->d_state->status, 0, sizeof(unsigned)));
+    if (device_status) *device_status = st;
+    if (st & crk::ST_TIMEOUT) return fail(CRKDG_ETIMEOUT, "a bounded device wait ran out");
+    if (st) return fail(CRKDG_ENONPHYSICAL, "non-physical or NaN state seen on the device");
+    return CRKDG_OK;
+}
+
+int crkdg_time(const crkdg_ctx* cc, double* t) {
+    crkdg_ctx* c = const_cast<crkdg_ctx*>(cc);
+    if (check_ctx(c) || !t) return fail(CRKDG_EINVAL, "null argument");
+    if (!c->t_known) {
+        CK(cudaMemcpyAsync(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->t_known = true;
+    }
+    *t = c->t;
+    return CRKDG_OK;
+}
+
+int crkdg_set_launch(crkdg_ctx* c, int seg_rows, int wpb) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (seg_rows < 0 || wpb < 0) return fail(CRKDG_EINVAL, "negative launch shape");
+    if (wpb > 0) {
+        const int mx = max_wpb(c);
+        if (mx < 0) return mx;
+        if (wpb > mx) return fail(CRKDG_EINVAL, "warps per block exceeds the kernel's register/shared-memory limit");
+        c->wpb = wpb;
+    }
+    if (seg_rows > 0) c->seg_rows = std::min(seg_rows, c->mesh.ny);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return CRKDG_OK;
+}
+
+int crkdg_get_launch(const crkdg_ctx* c, int* seg_rows, int* wpb) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (seg_rows) *seg_rows = c->seg_rows;
+    if (wpb) *wpb = c->wpb;
+    return CRKDG_OK;
+}
+
+int crkdg_autotune(crkdg_ctx* c, double* best_us) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "autotune is for the 2D step");
+    // time candidate shapes on the current state; u[cur] is only read, the
+    // device run state is saved and restored around the trials
+    DevState saved;
+    CK(cudaMemcpy(&saved, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost));
+    const int mx = max_wpb(c);
+    if (mx < 0) return mx;
+    const int rows[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96};
+    const int wpbs[] = {1, 2, 4, 8};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e30;
+    int bl = c->seg_rows, bw = c->wpb;
+    const int cur0 = c->cur;
+    double dt = 0.0;
+    {
+        int r = enqueue_reduce(c, 0);
+        if (r) return r;
+        double ms = 0.0;
+        CK(cudaMemcpy(&ms, &c->d_state->maxspeed, sizeof(double), cudaMemcpyDeviceToHost));
+        dt = ms > 0 ? 0.05 / ms : 1e-6;
+    }
+    for (int L : rows) {
+        if (L > c->mesh.ny && L != rows[0]) continue;
+        for (int w : wpbs) {
+            if (w > mx) continue;
+            c->seg_rows = std::min(L, c->mesh.ny);
+            c->wpb = w;
+            float tot = 0.f;
+            for (int it = 0; it < 4; ++it) {
+                c->cur = cur0;
+                CK(cudaEventRecord(e0, c->stream));
+                int r = enqueue_step(c, dt, 0, c->pending, c->M_pending);
+                if (r) return r;
+                CK(cudaEventRecord(e1, c->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (it > 0) tot += ms;
+            }
+            const double us = 1000.0 * tot / 3.0;
+            if (us < best) {
+                best = us;
+                bl = c->seg_rows;
+                bw = w;
+            }
+        }
+    }
+    c->cur = cur0;
+    c->seg_rows = bl;
+    c->wpb = bw;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpy(c->d_state, &saved, sizeof(DevState), cudaMemcpyHostToDevice));
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    if (best_us) *best_us = best;
+    return CRKDG_OK;
+}
+
+int crkdg_save(crkdg_ctx* c, const char* path) {
+    if (check_ctx(c) || !path) return fail(CRKDG_EINVAL, "null argument");
+    std::vector<double> h(c->elems);
+    const bool pend = c->pending;
+    const double Mp = c->M_pending;
+    // save the stored (not yet limited) state and the pending flag
+    c->pending = false;
+    int r = crkdg_get_state(c, h.data());
+    c->pending = pend;
+    if (r) return r;
+    double t;
+    r = crkdg_time(c, &t);
+    if (r) return r;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(CRKDG_EINVAL, std::string("cannot open ") + path);
+    const int hdr[8] = {0x43524b44, 1, c->dim, c->mesh.nx, c->mesh.ny, c->nv, c->nm, c->precision};
+    const double dh[4] = {t, pend ? 1.0 : 0.0, Mp, c->limiter_on ? c->M : -1.0};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(dh, sizeof(dh), 1, f) == 1 &&
+              std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? CRKDG_OK : fail(CRKDG_EINVAL, "write failed");
+}
+
+int crkdg_load(crkdg_ctx* c, const char* path) {
+    if (check_ctx(c) || !path) return fail(CRKDG_EINVAL, "null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(CRKDG_EINVAL, std::string("cannot open ") + path);
+    int hdr[8];
+    double dh[4];
+    std::vector<double> h(c->elems);
+    bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(dh, sizeof(dh), 1, f) == 1;
+    ok = ok && hdr[0] == 0x43524b44 && hdr[2] == c->dim && hdr[3] == c->mesh.nx && hdr[4] == c->mesh.ny &&
+         hdr[5] == c->nv && hdr[6] == c->nm;
+    ok = ok && std::fread(h.data(), sizeof(double), h.size(), f) == h.size();
+    std::fclose(f);
+    if (!ok) return fail(CRKDG_EINVAL, "checkpoint does not match this context");
+    int r = crkdg_set_state(c, h.data(), dh[0]);
+    if (r) return r;
+    c->pending = dh[1] != 0.0;
+    c->M_pending = dh[2];
+    c->limiter_on = dh[3] >= 0.0;
+    c->M = dh[3];
+    return CRKDG_OK;
+}
+
+}  // extern "C"

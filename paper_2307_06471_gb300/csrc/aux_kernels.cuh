@@ -1,0 +1,186 @@
+// Auxiliary kernels: FP64 reductions of the cell averages (CFL wave speed and
+// conserved totals, eq. (3.4)), the L2 projection of point values onto the
+// modal basis (the Pi of Sec. 2.2) and the standalone TVB limiter.
+#pragma once
+#include "common.cuh"
+#include "limiter.cuh"
+
+namespace crk {
+
+// max_K wave speed (2D: s_x/dx + s_y/dy; 1D: |f'|/dx) and sum_K |K| ubar_K,
+// from the mode-0 planes.  Per-warp slots, then the last warp reduces them in
+// a fixed order (deterministic) and writes DevState.
+template <class T, int PHYS, int NV>
+__global__ void reduce_state_kernel(const T* __restrict__ u, int nx, int ny, int nm, double dx, double dy,
+                                    double gamma, double bx, double by, DevState* ds, double* partials,
+                                    int set_dt) {
+    const size_t plane = (size_t)nx * ny;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int total_warps = gridDim.x * (blockDim.x >> 5);
+    double mx = 0.0, sm[NV];
+    unsigned st = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm[v] = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < plane; c += (size_t)gridDim.x * blockDim.x) {
+        double av[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            av[v] = double(u[(size_t)(v * nm) * plane + c]);
+            sm[v] += av[v];
+        }
+        double sp;
+        if constexpr (PHYS == PHYS_EULER) {
+            const double ir = 1.0 / av[0];
+            const double w = av[1] * ir, v = av[2] * ir;
+            const double p = (gamma - 1.0) * (av[3] - 0.5 * (av[1] * w + av[2] * v));
+            const double cs = sqrt(fmax(gamma * p * ir, 0.0));
+            sp = (fabs(w) + cs) / dx + (fabs(v) + cs) / dy;
+            if (!(av[0] > 0.0) || !(p > 0.0)) st |= ST_NONPHYSICAL;
+        } else if constexpr (PHYS == PHYS_EULER1D) {
+            const double ir = 1.0 / av[0];
+            const double w = av[1] * ir;
+            const double p = (gamma - 1.0) * (av[2] - 0.5 * av[1] * w);
+            sp = (fabs(w) + sqrt(fmax(gamma * p * ir, 0.0))) / dx;
+            if (!(av[0] > 0.0) || !(p > 0.0)) st |= ST_NONPHYSICAL;
+        } else {
+            sp = fabs(bx) / dx + (ny > 1 ? fabs(by) / dy : 0.0);
+        }
+        if (!(sp == sp)) st |= ST_NAN;
+        mx = fmax(mx, sp);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm[v] += __shfl_xor_sync(0xffffffffu, sm[v], off);
+        st |= __shfl_xor_sync(0xffffffffu, st, off);
+    }
+    unsigned prev = 0;
+    if (lane == 0) {
+        double* q = partials + (size_t)gw * (NV + 2);
+        q[0] = mx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q[1 + v] = sm[v] * dx * dy;
+        if (st) atomicOr(&ds->status, st);
+        __threadfence();
+        prev = atomicAdd(&ds->counter, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned)total_warps - 1) return;
+    __threadfence();
+    double M = 0.0, Sm[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Sm[v] = 0.0;
+    for (int wi = lane; wi < total_warps; wi += 32) {
+        const double* q = partials + (size_t)wi * (NV + 2);
+        M = fmax(M, __ldcg(q));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Sm[v] += __ldcg(q + 1 + v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        M = fmax(M, __shfl_xor_sync(0xffffffffu, M, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Sm[v] += __shfl_xor_sync(0xffffffffu, Sm[v], off);
+    }
+    if (lane == 0) {
+        ds->maxspeed = M;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ds->sums[v] = Sm[v];
+        if (set_dt) {
+            double d = ds->cfl > 0.0 && M > 0.0 ? ds->cfl / M : 0.0;
+            const double rem = ds->t_end - ds->t;
+            ds->dt = d < rem ? d : rem;
+        }
+        ds->counter = 0;
+    }
+}
+
+// u_m = sum_q pw[q][m] g(x_q) per cell, values[cell][q][v] (FP64, device).
+template <class T, int K, int B, int NV>
+__global__ void project2d_kernel(const double* __restrict__ vals, T* __restrict__ u, int ncell) {
+    constexpr Tab2D<K, B> tb = make_tab2d<K, B>();
+    constexpr int NQV = Tab2D<K, B>::NQV, NM = Tab2D<K, B>::NM;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const size_t plane = ncell;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) s += tb.pw[q][m] * vals[((size_t)c * NQV + q) * NV + v];
+            u[(size_t)(v * NM + m) * plane + c] = T(s);
+        }
+}
+
+template <class T, int K, int NV>
+__global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict__ u, int ncell) {
+    constexpr Tab1D<K> tb = make_tab1d<K>();
+    constexpr int NQ = K + 1, NM = K + 1;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s += tb.pw[q][m] * vals[((size_t)c * NQ + q) * NV + v];
+            u[(size_t)(v * NM + m) * ncell + c] = T(s);
+        }
+}
+
+// Standalone TVB limiter, in place: a thread reads its own modes and the
+// neighbours' averages (mode 0) and writes only its own modes 1.. , so no
+// thread writes anything another thread reads.  Counts troubled cells.
+template <class T, int K, int B, int PHYS>
+__global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned long long* flag_count) {
+    constexpr int NM = Tab2D<K, B>::NM;
+    constexpr int NV = Phys<T, PHYS>::NV;
+    const int nx = a.nx, ny = a.ny;
+    const size_t plane = (size_t)nx * ny;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    bool fl = false;
+    if (x < nx) {
+        const bool perx = a.bc[0].type == BC_PERIODIC, pery = a.bc[2].type == BC_PERIODIC;
+        T c[NV][NM];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) c[v][m] = u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x];
+        T own[NV], nb[4][NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) own[v] = c[v][0];
+        const int xx[4] = {x - 1, x + 1, x, x};
+        const int yy[4] = {y, y, y - 1, y + 1};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int cx = xx[s], cy = yy[s];
+            const bool out = (s < 2 && !perx && (cx < 0 || cx >= nx)) || (s >= 2 && !pery && (cy < 0 || cy >= ny));
+            if (out) {
+                const double xc = a.x0 + (cx + 0.5) * a.dx, yc = a.y0 + (cy + 0.5) * a.dy;
+                bc_exterior<T, NV>(a.bc[s], s < 2 ? 0 : 1, own, xc, yc, a.t, nb[s]);
+            } else {
+                cx = (cx + nx) % nx;
+                cy = (cy + ny) % ny;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) nb[s][v] = u[(size_t)(v * NM) * plane + (size_t)cy * nx + cx];
+            }
+        }
+        fl = tvb_limit_cell<T, NV, NM>(c, nb[0], nb[1], nb[2], nb[3], T(a.M * a.dx * a.dx), T(a.M * a.dy * a.dy),
+                                       T(a.gamma));
+        if (fl)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x] = c[v][m];
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, fl);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
+}
+
+}  // namespace crk

@@ -1,0 +1,188 @@
+// Shared device definitions: launch arguments, device state, physical
+// fluxes, the Lax--Friedrichs flux (Sec. 2.1) and boundary exterior states.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tables.cuh"
+
+namespace crk {
+
+constexpr int MAXS = 6;
+enum { PHYS_ADV = 0, PHYS_EULER = 1, PHYS_EULER1D = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
+enum { FN_CONST = 0, FN_SINE = 1, FN_SINE_PROD = 2, FN_DMR_BOTTOM = 3, FN_DMR_TOP = 4 };
+enum { ST_NONPHYSICAL = 1u, ST_NAN = 2u, ST_TIMEOUT = 4u };
+
+// Device-resident run state.  The fused reduction of every step writes the
+// FP64 wave-speed maximum and totals of the new cell averages here and, for
+// device-driven runs, the next dt = min(cfl / maxspeed, t_end - t).
+struct DevState {
+    double t, dt, t_end, cfl;
+    double maxspeed;
+    double sums[4];
+    double troubled;          // troubled cells flagged in the last step
+    unsigned status;          // ST_* bits
+    unsigned counter;         // arrival counter of the last-warp reduction
+    unsigned long long steps;
+};
+
+struct BCSide {
+    int type;
+    int fn;
+    double p[16];
+};
+
+struct StepArgs {
+    const void* uin;
+    void* uout;
+    int nx, ny;
+    double x0, y0, dx, dy;
+    double t, dt;             // used when dt_from_dev == 0
+    int dt_from_dev;
+    DevState* ds;
+    double* partials;         // per-warp reduction slots
+    int s;
+    const double* tab;        // device: a[MAXS*MAXS] row-major, b[MAXS], c[MAXS]
+    BCSide bc[4];             // W, E, S, N
+    int seg_len, n_strips, n_segs;
+    int limit;                // 1: limit u^n on load with TVB parameter M
+    double M;
+    double gamma;
+    double beta[2];
+};
+
+// -------------------------------------------------------------------------
+// Physical flux along one axis and the wave speed |f'(u).nu| for nu = e_axis.
+template <class T, int PHYS> struct Phys;
+
+template <class T> struct Phys<T, PHYS_ADV> {
+    static constexpr int NV = 1;
+    T bx, by;
+    __device__ __forceinline__ void flux2(const T* u, T* fx, T* fy) const {
+        fx[0] = bx * u[0];
+        fy[0] = by * u[0];
+    }
+    template <int AXIS>
+    __device__ __forceinline__ T fluxn(const T* u, T* f) const {
+        const T b = AXIS == 0 ? bx : by;
+        f[0] = b * u[0];
+        return fabs(b);
+    }
+};
+
+template <class T> struct Phys<T, PHYS_EULER> {
+    static constexpr int NV = 4;
+    T gm1, gamma;
+    __device__ __forceinline__ void flux2(const T* u, T* fx, T* fy) const {
+        const T ir = T(1) / u[0];
+        const T w = u[1] * ir, v = u[2] * ir;
+        const T p = gm1 * (u[3] - T(0.5) * (u[1] * w + u[2] * v));
+        const T ep = u[3] + p;
+        fx[0] = u[1]; fx[1] = u[1] * w + p; fx[2] = u[2] * w; fx[3] = w * ep;
+        fy[0] = u[2]; fy[1] = u[1] * v; fy[2] = u[2] * v + p; fy[3] = v * ep;
+    }
+    // normal flux and wave speed |v_n| + c
+    template <int AXIS>
+    __device__ __forceinline__ T fluxn(const T* u, T* f) const {
+        const T ir = T(1) / u[0];
+        const T w = u[1] * ir, v = u[2] * ir;
+        const T p = gm1 * (u[3] - T(0.5) * (u[1] * w + u[2] * v));
+        const T vn = AXIS == 0 ? w : v;
+        f[0] = u[1 + AXIS];
+        f[1] = u[1] * vn + (AXIS == 0 ? p : T(0));
+        f[2] = u[2] * vn + (AXIS == 1 ? p : T(0));
+        f[3] = vn * (u[3] + p);
+        const T c2 = gamma * p * ir;
+        return fabs(vn) + sqrt(c2 > T(0) ? c2 : T(0));
+    }
+};
+
+// 1D Euler: (rho, rho w, E)
+template <class T> struct Phys<T, PHYS_EULER1D> {
+    static constexpr int NV = 3;
+    T gm1, gamma;
+    template <int AXIS>
+    __device__ __forceinline__ T fluxn(const T* u, T* f) const {
+        const T ir = T(1) / u[0];
+        const T w = u[1] * ir;
+        const T p = gm1 * (u[2] - T(0.5) * u[1] * w);
+        f[0] = u[1];
+        f[1] = u[1] * w + p;
+        f[2] = w * (u[2] + p);
+        const T c2 = gamma * p * ir;
+        return fabs(w) + sqrt(c2 > T(0) ? c2 : T(0));
+    }
+};
+
+// Lax--Friedrichs flux through a face with normal +e_AXIS from the state on
+// the low side uL to the state on the high side uR; alpha is local to the
+// point: max of |f'.nu| over both traces.
+template <class T, int PHYS, int AXIS>
+__device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const T* uR, T* F) {
+    constexpr int NV = Phys<T, PHYS>::NV;
+    T fL[NV], fR[NV];
+    const T sL = ph.template fluxn<AXIS>(uL, fL);
+    const T sR = ph.template fluxn<AXIS>(uR, fR);
+    const T al = sL > sR ? sL : sR;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+}
+
+// Exterior state at a boundary point (x, y) and time t from the interior
+// state; AXIS is the axis normal to the boundary.
+template <class T, int NV>
+__device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T* uin, double x, double y,
+                                            double t, T* uext) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) uext[v] = uin[v];
+    if (bc.type == BC_OUTFLOW) return;
+    if (bc.type == BC_REFLECT) {
+        if (NV >= 3) uext[1 + axis] = -uin[1 + axis];
+        return;
+    }
+    const double* p = bc.p;
+    switch (bc.fn) {
+        case FN_CONST:
+#pragma unroll
+            for (int v = 0; v < NV; ++v) uext[v] = T(p[v]);
+            break;
+        case FN_SINE:
+            uext[0] = T(p[0] * sin(p[1] * x + p[2] * y - p[3] * t + p[4]));
+            break;
+        case FN_SINE_PROD:
+            uext[0] = T(p[0] * sin(p[1] * (x - p[2] * t)) * sin(p[3] * (y - p[4] * t)));
+            break;
+        case FN_DMR_BOTTOM:
+            if (x < p[4]) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) uext[v] = T(p[v]);
+            } else if (NV >= 3) {
+                uext[1 + axis] = -uin[1 + axis];
+            }
+            break;
+        case FN_DMR_TOP: {
+            const double xs = p[8] + p[9] * y + p[10] * t;
+            const double* st = x < xs ? p : p + 4;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) uext[v] = T(st[v]);
+        } break;
+        default:
+            break;
+    }
+}
+
+__device__ __forceinline__ double tab_a(const StepArgs& a, int i, int j) { return __ldg(a.tab + i * MAXS + j); }
+__device__ __forceinline__ double tab_b(const StepArgs& a, int i) { return __ldg(a.tab + MAXS * MAXS + i); }
+__device__ __forceinline__ double tab_c(const StepArgs& a, int i) { return __ldg(a.tab + MAXS * MAXS + MAXS + i); }
+
+template <class T>
+__device__ __forceinline__ T shfl_down(T v, int d) {
+    return __shfl_down_sync(0xffffffffu, v, d);
+}
+template <class T>
+__device__ __forceinline__ T shfl_up(T v, int d) {
+    return __shfl_up_sync(0xffffffffu, v, d);
+}
+
+}  // namespace crk

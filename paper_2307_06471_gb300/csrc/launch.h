@@ -1,0 +1,47 @@
+// Internal launcher interface between the C ABI (api.cu) and the kernel
+// translation units (one per physics x precision, compiled in parallel).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace crk {
+
+struct KernelInfo {
+    int regs;              // registers per thread of the step kernel
+    int max_threads;       // max threads per block it can launch with
+    int smem_per_thread;   // bytes of private shared memory per thread (for a.s stages)
+};
+
+// 2D fused step (step2d.cuh); wpb = warps per block
+cudaError_t launch_step2d(int phys, int prec, int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t info_step2d(int phys, int prec, int k, int basis, int s, KernelInfo* info);
+// standalone TVB limiter (in place)
+cudaError_t launch_limit2d(int phys, int prec, int k, int basis, const StepArgs& a, void* u,
+                           unsigned long long* flags, cudaStream_t st);
+// projection of point values (device FP64 [cell][q][v])
+cudaError_t launch_project(int dim, int phys, int prec, int k, int basis, const double* vals, void* u, int ncell,
+                           cudaStream_t st);
+// 1D fused step; n_steps > 1 requires one block
+cudaError_t launch_step1d(int phys, int prec, int k, const StepArgs& a, int n_steps, int threads, int blocks,
+                          cudaStream_t st);
+cudaError_t info_step1d(int phys, int prec, int k, int s, KernelInfo* info);
+// FP64 reduction of the averages into DevState (set_dt: also dt = cfl/max)
+cudaError_t launch_reduce(int dim, int phys, int prec, const void* u, int nx, int ny, int nm, double dx, double dy,
+                          double gamma, double bx, double by, DevState* ds, double* partials, int blocks, int set_dt,
+                          cudaStream_t st);
+
+// per-(phys, prec) entry points defined in the kernel translation units
+#define CRK_DECL_2D(NAME)                                                                                  \
+    cudaError_t step2d_##NAME(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);            \
+    cudaError_t info2d_##NAME(int k, int basis, int s, KernelInfo* info);                                \
+    cudaError_t limit2d_##NAME(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,  \
+                               cudaStream_t st);                                                         \
+    cudaError_t project2d_##NAME(int k, int basis, const double* vals, void* u, int ncell, cudaStream_t st);
+CRK_DECL_2D(euler_f32)
+CRK_DECL_2D(euler_f64)
+CRK_DECL_2D(adv_f32)
+CRK_DECL_2D(adv_f64)
+#undef CRK_DECL_2D
+
+}  // namespace crk

@@ -1,0 +1,167 @@
+// TVB-minmod limiter in characteristic fields on Cartesian cells (Sec. 4.2,
+// Remark 2.2; the limiter of Cockburn and Shu for multidimensional systems,
+// which the paper cites without printing it).  Reading implemented:
+//   per direction (x: slope mode (1,0), neighbours E/W, mesh size dx;
+//                  y: slope mode (0,1), neighbours N/S, mesh size dy):
+//     a1 = slope coefficient, a2 = ubar_E - ubar, a3 = ubar - ubar_W,
+//     projected on characteristic fields with L = R^{-1} at the cell average
+//     (scalar problems: no projection);
+//     mt = a1 if |a1| <= M h^2 else minmod(a1, a2, a3)
+//   troubled if mt != a1 in any field of either direction; then the slope
+//   modes become R mt, every other non-constant mode becomes 0, and the
+//   average is kept.
+#pragma once
+#include "common.cuh"
+
+namespace crk {
+
+template <class T>
+__device__ __forceinline__ T minmod3(T a, T b, T c) {
+    const bool pos = a > T(0) && b > T(0) && c > T(0);
+    const bool neg = a < T(0) && b < T(0) && c < T(0);
+    T m = fabs(a);
+    m = fabs(b) < m ? fabs(b) : m;
+    m = fabs(c) < m ? fabs(c) : m;
+    return pos ? m : (neg ? -m : T(0));
+}
+
+template <class T>
+__device__ __forceinline__ T tvb_minmod(T a1, T a2, T a3, T Mh2) {
+    return fabs(a1) <= Mh2 ? a1 : minmod3(a1, a2, a3);
+}
+
+// Left (L) and right (R) eigenvectors of the 2D Euler flux Jacobian along
+// AXIS at state u; R columns for eigenvalues (vn - c, vn, vn, vn + c).
+template <class T, int AXIS>
+__device__ __forceinline__ void euler_eig(const T* u, T gamma, T R[4][4], T L[4][4]) {
+    const T gm1 = gamma - T(1);
+    const T ir = T(1) / u[0];
+    const T w = u[1] * ir, v = u[2] * ir;
+    const T q2 = w * w + v * v;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    const T c2 = gamma * p * ir;
+    const T c = sqrt(c2 > T(0) ? c2 : T(0));
+    const T H = (u[3] + p) * ir;
+    const T vn = AXIS == 0 ? w : v;   // normal velocity
+    const T vt = AXIS == 0 ? v : w;   // tangential velocity
+    const int in = 1 + AXIS;          // normal momentum index
+    const int it = 2 - AXIS;          // tangential momentum index
+    // right eigenvectors (columns)
+    R[0][0] = T(1); R[0][1] = T(1); R[0][2] = T(0); R[0][3] = T(1);
+    R[in][0] = vn - c; R[in][1] = vn; R[in][2] = T(0); R[in][3] = vn + c;
+    R[it][0] = vt; R[it][1] = vt; R[it][2] = T(1); R[it][3] = vt;
+    R[3][0] = H - vn * c; R[3][1] = T(0.5) * q2; R[3][2] = vt; R[3][3] = H + vn * c;
+    // left eigenvectors (rows of R^{-1})
+    const T ic = T(1) / c;
+    const T b1 = gm1 * ic * ic;
+    const T b2 = T(0.5) * b1 * q2;
+    const T wv[2] = {w, v};
+    // acoustic (vn - c)
+    L[0][0] = T(0.5) * (b2 + vn * ic);
+    L[0][in] = -T(0.5) * (b1 * vn + ic);
+    L[0][it] = -T(0.5) * b1 * vt;
+    L[0][3] = T(0.5) * b1;
+    // entropy
+    L[1][0] = T(1) - b2;
+    L[1][in] = b1 * vn;
+    L[1][it] = b1 * vt;
+    L[1][3] = -b1;
+    // shear
+    L[2][0] = -vt;
+    L[2][in] = T(0);
+    L[2][it] = T(1);
+    L[2][3] = T(0);
+    // acoustic (vn + c)
+    L[3][0] = T(0.5) * (b2 - vn * ic);
+    L[3][in] = -T(0.5) * (b1 * vn - ic);
+    L[3][it] = -T(0.5) * b1 * vt;
+    L[3][3] = T(0.5) * b1;
+    (void)wv;
+}
+
+// Limit one cell in place.  u[v][m] modal coefficients, nb* neighbour
+// averages.  Returns true if the cell was troubled.
+template <class T, int NV, int NM>
+__device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, const T* nbE, const T* nbS,
+                                               const T* nbN, T Mdx2, T Mdy2, T gamma) {
+    if (NM < 3) return false;
+    T avg[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) avg[v] = u[v][0];
+    T mx[NV], my[NV];
+    bool flag = false;
+    if (NV == 4) {
+        T R[4][4], L[4][4];
+        // x direction
+        euler_eig<T, 0>(avg, gamma, R, L);
+        T c1[4], c2[4], c3[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            T s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                s1 += L[f][v] * u[v][1];
+                s2 += L[f][v] * (nbE[v] - avg[v]);
+                s3 += L[f][v] * (avg[v] - nbW[v]);
+            }
+            c1[f] = s1; c2[f] = s2; c3[f] = s3;
+        }
+        T m[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            m[f] = tvb_minmod(c1[f], c2[f], c3[f], Mdx2);
+            flag |= (m[f] != c1[f]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            T s = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s += R[v][f] * m[f];
+            mx[v] = s;
+        }
+        // y direction
+        euler_eig<T, 1>(avg, gamma, R, L);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            T s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                s1 += L[f][v] * u[v][2];
+                s2 += L[f][v] * (nbN[v] - avg[v]);
+                s3 += L[f][v] * (avg[v] - nbS[v]);
+            }
+            c1[f] = s1; c2[f] = s2; c3[f] = s3;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            m[f] = tvb_minmod(c1[f], c2[f], c3[f], Mdy2);
+            flag |= (m[f] != c1[f]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            T s = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s += R[v][f] * m[f];
+            my[v] = s;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            mx[v] = tvb_minmod(u[v][1], nbE[v] - avg[v], avg[v] - nbW[v], Mdx2);
+            my[v] = tvb_minmod(u[v][2], nbN[v] - avg[v], avg[v] - nbS[v], Mdy2);
+            flag |= (mx[v] != u[v][1]) || (my[v] != u[v][2]);
+        }
+    }
+    if (flag) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            u[v][1] = mx[v];
+            u[v][2] = my[v];
+#pragma unroll
+            for (int m = 3; m < NM; ++m) u[v][m] = T(0);
+        }
+    }
+    return flag;
+}
+
+}  // namespace crk

@@ -1,0 +1,528 @@
+// Fused cRKDG time step on a 2D Cartesian mesh (eq. (2.8)).
+//
+// Work decomposition ("marching warps"): a warp owns a strip of 30 columns
+// plus one halo column on each side (lane l holds column x0 - 1 + l) and
+// marches up a segment of rows.  For every row each lane
+//   1. loads u^n of its cell (planes [v][m][y][x]: one coalesced 128-byte
+//      line per (v, m) for the warp) and, if a limit is pending, applies the
+//      TVB limiter of the previous step to it (limit-on-load);
+//   2. runs every RK stage cell-locally (eq. (2.8), first line): stage states
+//      u^(i) and div^loc f(u^(i)) (eq. (2.7)) stay in registers and in the
+//      thread's private shared-memory slots; nothing of a stage reaches HBM;
+//   3. forms the final-stage face fluxes sum_i b_i fhat(u^(i)) (eq. (2.8),
+//      second line): east/west faces with the neighbouring lane through
+//      warp shuffles, south faces with the north traces of the row below,
+//      kept per stage in the same thread's shared-memory slot;
+//   4. completes the update of the row below (its north face is the current
+//      row's south face) and writes u^{n+1} of that row once.
+// Halo columns and one extra row at each segment end are recomputed instead
+// of exchanged: the compactness of cRKDG (Sec. 3.1) means one ring suffices.
+// Boundary data enter only the final-stage fluxes, at t^n + c_i dt (Sec. 3.4).
+// The FP64 epilogue reduces the new cell averages (max wave speed, totals;
+// eq. (3.4)) with a last-warp-done pass and updates the device run state.
+#pragma once
+#include "common.cuh"
+#include "limiter.cuh"
+
+namespace crk {
+
+template <class T, int K, int B, int PHYS>
+struct Step2D {
+    using TB = Tab2D<K, B>;
+    static constexpr int NQ = TB::NQ;
+    static constexpr int NQV = TB::NQV;
+    static constexpr int NM = TB::NM;
+    static constexpr int NV = Phys<T, PHYS>::NV;
+    static constexpr int NDOF = NV * NM;
+    static constexpr int NRED = NV + 2;   // reduction slots: maxspeed, sums[NV], troubled
+
+    // T elements of private shared memory per thread for s stages
+    static __host__ __device__ constexpr int smem_per_thread(int s) {
+        return (s - 1) * NDOF + s * NQ * NV + NDOF;
+    }
+};
+
+template <class T, int K, int B, int PHYS>
+__global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
+    using C = Step2D<T, K, B, PHYS>;
+    using TBL = typename C::TB;
+    constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
+    constexpr TBL tb = make_tab2d<K, B>();
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int S = a.s;
+    const int offN = (S - 1) * C::NDOF;
+    const int offP = offN + S * NQ * NV;
+    auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
+
+    const int lane = tid & 31;
+    const int gw = blockIdx.x * (nthr >> 5) + (tid >> 5);
+    const int total_warps = a.n_strips * a.n_segs;
+    if (gw >= total_warps) return;   // whole warp leaves; no block barriers below
+
+    const int nx = a.nx, ny = a.ny;
+    const size_t plane = (size_t)nx * ny;
+    const T* __restrict__ uin = static_cast<const T*>(a.uin);
+    T* __restrict__ uout = static_cast<T*>(a.uout);
+
+    const double dt = a.dt_from_dev ? a.ds->dt : a.dt;
+    const double t0 = a.dt_from_dev ? a.ds->t : a.t;
+
+    const int strip = gw % a.n_strips;
+    const int seg = gw / a.n_strips;
+    const int xs = strip * 30;
+    const int col = xs - 1 + lane;
+    const bool perx = a.bc[0].type == BC_PERIODIC;
+    const bool pery = a.bc[2].type == BC_PERIODIC;
+    int xl = ((col % nx) + nx) % nx;
+    if (!perx) xl = col < 0 ? 0 : (col >= nx ? nx - 1 : col);
+    const bool outlane = lane >= 1 && lane <= 30 && col < nx;
+    const bool has_bcW = !perx && xs == 0;
+    const bool has_bcE = !perx && xs + 30 >= nx;
+
+    const int r0 = seg * a.seg_len;
+    const int r1 = min(r0 + a.seg_len, ny);
+    const int rstart = (r0 > 0 || pery) ? r0 - 1 : r0;
+    const int rend = (r1 < ny || pery) ? r1 : r1 - 1;
+
+    // a non-positive dt leaves the state unchanged (runs past t_end)
+    if (!(dt > 0.0)) {
+        if (outlane)
+            for (int r = r0; r < r1; ++r)
+                for (int d = 0; d < C::NDOF; ++d) uout[d * plane + (size_t)r * nx + col] = uin[d * plane + (size_t)r * nx + col];
+        return;
+    }
+
+    Phys<T, PHYS> ph;
+    if constexpr (PHYS == PHYS_EULER) {
+        ph.gamma = T(a.gamma);
+        ph.gm1 = T(a.gamma - 1.0);
+    } else {
+        ph.bx = T(a.beta[0]);
+        ph.by = T(a.beta[1]);
+    }
+    const T rx = T(1.0 / a.dx), ry = T(1.0 / a.dy);
+    const T tdt = T(dt);
+    const T Mdx2 = T(a.M * a.dx * a.dx), Mdy2 = T(a.M * a.dy * a.dy);
+    const T gam = T(a.gamma);
+
+    // reduction accumulators (FP64)
+    double red_max = 0.0;
+    double red_sum[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red_sum[v] = 0.0;
+    unsigned red_trouble = 0;
+    unsigned status = 0;
+
+    // limiter: rolling neighbour averages of this column
+    T avg_prev[NV], avg_next[NV];
+    auto load_avg = [&](int r, T* out) {
+        // average of (column xl, row r), r in [-1, ny]; beyond a non-periodic
+        // side: ghost average from the boundary cell (at time t^n)
+        int rr = r;
+        bool ghost = false;
+        if (r < 0) { if (pery) rr = r + ny; else { rr = 0; ghost = true; } }
+        if (r >= ny) { if (pery) rr = r - ny; else { rr = ny - 1; ghost = true; } }
+        T own[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) own[v] = uin[(size_t)(v * NM) * plane + (size_t)rr * nx + xl];
+        if (!ghost) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] = own[v];
+        } else {
+            const int side = r < 0 ? 2 : 3;
+            const double xc = a.x0 + (col + 0.5) * a.dx;
+            const double yc = r < 0 ? a.y0 - 0.5 * a.dy : a.y0 + (ny + 0.5) * a.dy;
+            bc_exterior<T, NV>(a.bc[side], 1, own, xc, yc, t0, out);
+        }
+    };
+    auto load_avg_x = [&](int c, int r, T* out) {
+        // average of column c (may be -1 .. nx) in row r (0..ny-1)
+        T own[NV];
+        int cc = perx ? ((c % nx) + nx) % nx : (c < 0 ? 0 : (c >= nx ? nx - 1 : c));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) own[v] = uin[(size_t)(v * NM) * plane + (size_t)r * nx + cc];
+        if (perx || (c >= 0 && c < nx)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] = own[v];
+        } else {
+            const int side = c < 0 ? 0 : 1;
+            const double xc = c < 0 ? a.x0 - 0.5 * a.dx : a.x0 + (nx + 0.5) * a.dx;
+            const double yc = a.y0 + (r + 0.5) * a.dy;
+            bc_exterior<T, NV>(a.bc[side], 0, own, xc, yc, t0, out);
+        }
+    };
+    if (a.limit) load_avg(rstart - 1, avg_prev);
+
+    for (int r = rstart; r <= rend; ++r) {
+        const int ry_ = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const bool out_row = r >= r0 && r < r1;
+        const bool south_bc = (r == 0) && !pery;
+        const bool do_south = (r > rstart) || south_bc;   // flux through this row's south face
+        const bool keep_north = r < rend || (r == ny - 1 && !pery && out_row);
+        const double yc = a.y0 + (ry_ + 0.5) * a.dy;
+
+        // ---- load u^n (and limit on load) -------------------------------------
+        T un[NV][NM];
+        const size_t cidx = (size_t)ry_ * nx + xl;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) un[v][m] = uin[(size_t)(v * NM + m) * plane + cidx];
+
+        if (a.limit) {
+            T avg_cur[NV], nbW[NV], nbE[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) avg_cur[v] = un[v][0];
+            load_avg(r + 1, avg_next);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                nbE[v] = shfl_down(avg_cur[v], 1);
+                nbW[v] = shfl_up(avg_cur[v], 1);
+            }
+            if (lane == 0) load_avg_x(col - 1, ry_, nbW);
+            if (lane == 31) load_avg_x(col + 1, ry_, nbE);
+            if (!perx && col == 0) load_avg_x(-1, ry_, nbW);
+            if (!perx && col == nx - 1) load_avg_x(nx, ry_, nbE);
+            const bool real = perx ? true : (col >= 0 && col < nx);
+            bool fl = false;
+            if (real) fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam);
+            if (out_row && outlane && fl) ++red_trouble;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) avg_prev[v] = avg_cur[v];
+        }
+
+        // ---- stages ---------------------------------------------------------------
+        T V[NV][NM];      // sum_i b_i * volume term
+        T FE[NQ][NV];     // sum_i b_i fhat on the east face
+        T FS[NQ][NV];     // sum_i b_i fhat on the south face
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) V[v][m] = T(0);
+#pragma unroll
+        for (int p = 0; p < NQ; ++p)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FE[p][v] = FS[p][v] = T(0);
+
+        for (int i = 0; i < S; ++i) {
+            const double bid = tab_b(a, i);
+            const T bi = T(bid);
+            const bool need_L = i < S - 1;
+            const bool need_flux = bid != 0.0;
+            if (!need_L && !need_flux) continue;
+            const double ti = t0 + tab_c(a, i) * dt;
+            // stage state u^(i) = u^n - dt sum_{j<i} a_ij L_j
+            T w[NV][NM];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) w[v][m] = un[v][m];
+            for (int j = 0; j < i; ++j) {
+                const double aijd = tab_a(a, i, j);
+                if (aijd == 0.0) continue;
+                const T aij = T(aijd) * tdt;
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) w[v][m] -= aij * slot(j * C::NDOF + v * NM + m);
+            }
+            // volume term  sum_q w_q (rx f_x dphi/dxi + ry f_y dphi/deta)
+            T vol[NV][NM];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) vol[v][m] = T(0);
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) {
+                T uq[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    T s = T(0);
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) s += w[v][m] * T(tb.phi[q][m]);
+                    uq[v] = s;
+                }
+                T fx[NV], fy[NV];
+                ph.flux2(uq, fx, fy);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const T gxv = rx * fx[v], gyv = ry * fy[v];
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        if (tb.gx[q][m] != 0.0) vol[v][m] += gxv * T(tb.gx[q][m]);
+                        if (tb.gy[q][m] != 0.0) vol[v][m] += gyv * T(tb.gy[q][m]);
+                    }
+                }
+            }
+            if (need_flux && out_row) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) V[v][m] += bi * vol[v][m];
+            }
+            // face traces
+            T tE[NQ][NV], tW[NQ][NV], tN[NQ][NV], tS[NQ][NV];
+#pragma unroll
+            for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    T e = 0, ww = 0, n = 0, s = 0;
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        e += w[v][m] * T(tb.tE[p][m]);
+                        ww += w[v][m] * T(tb.tW[p][m]);
+                        n += w[v][m] * T(tb.tN[p][m]);
+                        s += w[v][m] * T(tb.tS[p][m]);
+                    }
+                    tE[p][v] = e; tW[p][v] = ww; tN[p][v] = n; tS[p][v] = s;
+                }
+            // local operator L_i = cm (face_loc - vol), eq. (2.7)
+            if (need_L) {
+                T floc[NV][NM];
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) floc[v][m] = T(0);
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
+                    T fe[NV], fw[NV], fn[NV], fs[NV];
+                    ph.template fluxn<0>(tE[p], fe);
+                    ph.template fluxn<0>(tW[p], fw);
+                    ph.template fluxn<1>(tN[p], fn);
+                    ph.template fluxn<1>(tS[p], fs);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+#pragma unroll
+                        for (int m = 0; m < NM; ++m)
+                            floc[v][m] += rx * (fe[v] * T(tb.pE[p][m]) - fw[v] * T(tb.pW[p][m])) +
+                                          ry * (fn[v] * T(tb.pN[p][m]) - fs[v] * T(tb.pS[p][m]));
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m)
+                        slot(i * C::NDOF + v * NM + m) = T(tb.cm[m]) * (floc[v][m] - vol[v][m]);
+            }
+            if (!need_flux) continue;
+            // east face: own east trace vs. the west trace of the lane to the right
+            if (out_row) {
+                T tWn[NQ][NV];
+#pragma unroll
+                for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) tWn[p][v] = shfl_down(tW[p][v], 1);
+                if (has_bcW && lane == 0) {
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p)
+                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], a.x0, yc + 0.5 * a.dy * tb.xq[p], ti, tE[p]);
+                }
+                if (has_bcE && col == nx - 1) {
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p)
+                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], a.x0 + nx * a.dx, yc + 0.5 * a.dy * tb.xq[p], ti,
+                                           tWn[p]);
+                }
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
+                    T F[NV];
+                    llf<T, PHYS, 0>(ph, tE[p], tWn[p], F);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) FE[p][v] += bi * F[v];
+                }
+            }
+            // south face: north trace of the row below (stored) vs. own south trace
+            if (do_south) {
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
+                    T lo[NV];
+                    if (south_bc) {
+                        const double xp = a.x0 + (col + 0.5) * a.dx + 0.5 * a.dx * tb.xq[p];
+                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, a.y0, ti, lo);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
+                    }
+                    T F[NV];
+                    llf<T, PHYS, 1>(ph, lo, tS[p], F);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) FS[p][v] += bi * F[v];
+                }
+            }
+            if (keep_north) {
+#pragma unroll
+                for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) slot(offN + (i * NQ + p) * NV + v) = tN[p][v];
+            }
+        }
+
+        // ---- finish the row below: its north face is this row's south face --------
+        auto finish = [&](T (&P)[NV][NM], int rw) {
+            // write u^{n+1} of row rw and accumulate the FP64 reductions
+            if (!outlane) return;
+            const size_t o = (size_t)rw * nx + col;
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
+            double av[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                av[v] = double(P[v][0]);
+                red_sum[v] += av[v];
+            }
+            double sp;
+            if constexpr (PHYS == PHYS_EULER) {
+                const double ir = 1.0 / av[0];
+                const double w = av[1] * ir, vv = av[2] * ir;
+                const double p = (a.gamma - 1.0) * (av[3] - 0.5 * (av[1] * w + av[2] * vv));
+                const double c = sqrt(fmax(a.gamma * p * ir, 0.0));
+                sp = (fabs(w) + c) / a.dx + (fabs(vv) + c) / a.dy;
+                if (!(av[0] > 0.0) || !(p > 0.0)) status |= ST_NONPHYSICAL;
+                if (!(sp == sp)) status |= ST_NAN;
+            } else {
+                sp = fabs(a.beta[0]) / a.dx + fabs(a.beta[1]) / a.dy;
+                if (!(av[0] == av[0])) status |= ST_NAN;
+            }
+            red_max = fmax(red_max, sp);
+        };
+        if (do_south && r - 1 >= r0 && r - 1 < r1) {
+            T P[NV][NM];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    T s = T(0);
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p) s += FS[p][v] * T(tb.pN[p][m]);
+                    P[v][m] = slot(offP + v * NM + m) - tdt * T(tb.cm[m]) * (ry * s);
+                }
+            finish(P, r - 1);
+        }
+        if (!out_row) continue;
+
+        // ---- this row: east/west/south faces and the volume term ----------------------
+        T FW[NQ][NV];
+#pragma unroll
+        for (int p = 0; p < NQ; ++p)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FW[p][v] = shfl_up(FE[p][v], 1);
+        T P[NV][NM];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                T sx = T(0), sy = T(0);
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
+                    sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
+                    sy -= FS[p][v] * T(tb.pS[p][m]);
+                }
+                P[v][m] = un[v][m] - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V[v][m]);
+            }
+        if (r == ny - 1 && !pery) {
+            // top boundary: north face flux from the stored north traces
+            T FN[NQ][NV];
+#pragma unroll
+            for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) FN[p][v] = T(0);
+            for (int i = 0; i < S; ++i) {
+                const double bid = tab_b(a, i);
+                if (bid == 0.0) continue;
+                const T bi = T(bid);
+                const double ti = t0 + tab_c(a, i) * dt;
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
+                    T lo[NV], hi[NV], F[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
+                    const double xp = a.x0 + (col + 0.5) * a.dx + 0.5 * a.dx * tb.xq[p];
+                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, a.y0 + ny * a.dy, ti, hi);
+                    llf<T, PHYS, 1>(ph, lo, hi, F);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) FN[p][v] += bi * F[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    T s = T(0);
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p) s += FN[p][v] * T(tb.pN[p][m]);
+                    P[v][m] -= tdt * T(tb.cm[m]) * (ry * s);
+                }
+            finish(P, r);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) slot(offP + v * NM + m) = P[v][m];
+        }
+    }
+
+    // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
+    const double cell = a.dx * a.dy;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red_sum[v] += __shfl_xor_sync(0xffffffffu, red_sum[v], off);
+        red_trouble += __shfl_xor_sync(0xffffffffu, red_trouble, off);
+        status |= __shfl_xor_sync(0xffffffffu, status, off);
+    }
+    double* slotp = a.partials + (size_t)gw * C::NRED;
+    unsigned prev = 0;
+    if (lane == 0) {
+        slotp[0] = red_max;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
+        slotp[1 + NV] = double(red_trouble);
+        if (status) atomicOr(&a.ds->status, status);
+        __threadfence();
+        prev = atomicAdd(&a.ds->counter, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned)total_warps - 1) return;
+    // last warp: fixed-order reduction of all per-warp slots (deterministic)
+    __threadfence();
+    double mx = 0.0, sm_[NV], tr = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
+    for (int wi = lane; wi < total_warps; wi += 32) {
+        const double* q = a.partials + (size_t)wi * C::NRED;
+        mx = fmax(mx, __ldcg(q));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
+        tr += __ldcg(q + 1 + NV);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
+        tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    }
+    if (lane == 0) {
+        DevState* ds = a.ds;
+        ds->maxspeed = mx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
+        ds->troubled = tr;
+        const double tn = t0 + dt;
+        ds->t = tn;
+        double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
+        const double rem = ds->t_end - tn;
+        if (dn > rem) dn = rem;
+        ds->dt = dn;
+        ds->steps += 1;
+        ds->counter = 0;
+    }
+}
+
+}  // namespace crk

@@ -1,0 +1,125 @@
+"""Helpers that set up one problem on both sides of a parity test: the CUDA
+library through the C ABI (paper_2307_06471_gb300.binding) and the FP64 CPU
+oracle.  Boundary conditions are described once and translated to each
+side; layouts are converted between the oracle's u[y, x, v, m] and the
+library's planes [v, m, y, x].  Inputs come from crkdg_inputs only."""
+import numpy as np
+
+from oracle import tableaux as OTB
+from oracle.dg1d import DG1D
+from oracle.dg2d import DG2D
+from oracle.physics import Advection, Euler
+
+TAB_NAMES = {"midpoint": OTB.MIDPOINT, "heun2": OTB.HEUN, "heun3": OTB.HEUN3, "ssprk3": OTB.SSPRK3,
+             "rk4": OTB.RK4, "euler": OTB.EULER}
+
+
+def to_planes(u):
+    """oracle [y, x, v, m] (2D) or [x, v, m] (1D) -> library [v, m, y, x]."""
+    if u.ndim == 3:
+        return np.ascontiguousarray(np.transpose(u, (1, 2, 0))[:, :, None, :])
+    return np.ascontiguousarray(np.transpose(u, (2, 3, 0, 1)))
+
+
+def from_planes(p, dim=2):
+    if dim == 1:
+        return np.ascontiguousarray(np.transpose(p[:, :, 0, :], (2, 0, 1)))
+    return np.ascontiguousarray(np.transpose(p, (2, 3, 0, 1)))
+
+
+def _reflect(u, axis):
+    out = np.array(u, dtype=np.float64, copy=True)
+    out[..., 1 + axis] = -out[..., 1 + axis]
+    return out
+
+
+def gpu_bc(desc):
+    """(type, fn, params) of the C ABI for one side."""
+    from paper_2307_06471_gb300 import binding as B
+    kind = desc[0]
+    if kind == "periodic":
+        return B.BC_PERIODIC, 0, None
+    if kind == "outflow":
+        return B.BC_OUTFLOW, 0, None
+    if kind == "reflect":
+        return B.BC_REFLECT, 0, None
+    if kind == "const":
+        return B.BC_DIRICHLET, B.FN_CONST, list(desc[1])
+    if kind == "sine":
+        return B.BC_DIRICHLET, B.FN_SINE, list(desc[1:])
+    if kind == "sine_prod":
+        return B.BC_DIRICHLET, B.FN_SINE_PROD, list(desc[1:])
+    if kind == "dmr_bottom":
+        return B.BC_DIRICHLET, B.FN_DMR_BOTTOM, list(desc[1]) + [desc[2]]
+    if kind == "dmr_top":
+        return B.BC_DIRICHLET, B.FN_DMR_TOP, list(desc[1]) + list(desc[2]) + [desc[3], desc[4], desc[5]]
+    raise ValueError(desc)
+
+
+def oracle_bc(desc, axis):
+    kind = desc[0]
+    if kind in ("periodic", "outflow", "reflect"):
+        return kind
+    if kind == "const":
+        st = np.asarray(desc[1], dtype=np.float64)
+        return ("dirichlet", lambda X, Y, t: np.broadcast_to(st, np.shape(X) + st.shape).copy())
+    if kind == "sine":
+        A, kx, ky, w, ph = desc[1:]
+        return ("dirichlet", lambda X, Y, t: (A * np.sin(kx * X + ky * Y - w * t + ph))[..., None])
+    if kind == "sine_prod":
+        A, kx, cx, ky, cy = desc[1:]
+        return ("dirichlet", lambda X, Y, t: (A * np.sin(kx * (X - cx * t)) * np.sin(ky * (Y - cy * t)))[..., None])
+    if kind == "dmr_bottom":
+        post, x0 = np.asarray(desc[1]), desc[2]
+        return ("custom", lambda u, X, Y, t: np.where((np.asarray(X) < x0)[..., None], post, _reflect(u, axis)))
+    if kind == "dmr_top":
+        post, pre, x0, sy, st = np.asarray(desc[1]), np.asarray(desc[2]), desc[3], desc[4], desc[5]
+        return ("dirichlet", lambda X, Y, t: np.where((np.asarray(X) < x0 + sy * np.asarray(Y) + st * t)[..., None],
+                                                      post, pre))
+    raise ValueError(desc)
+
+
+def make_pair_2d(nx, ny, box, k, basis, physics, tab, bcs, precision, gamma=1.4, beta=(1.0, 0.5)):
+    """bcs: dict side -> description.  Returns (Solver, DG2D)."""
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    sides = ("W", "E", "S", "N")
+    codes = [gpu_bc(bcs[s]) for s in sides]
+    mesh = B.make_mesh(2, nx, ny, box, [c[0] for c in codes], [c[1] for c in codes], [c[2] for c in codes])
+    phys_id = B.EULER if physics == "euler" else B.ADVECTION
+    solver = B.Solver(mesh, k, B.BASIS_P if basis == "P" else B.BASIS_Q, GTB.BY_NAME[tab], phys_id,
+                      B.F64 if precision == "f64" else B.F32, gamma=gamma, beta=beta)
+    ph = Euler(gamma, 2) if physics == "euler" else Advection(list(beta))
+    obc = {s: oracle_bc(bcs[s], 0 if s in ("W", "E") else 1) for s in sides}
+    dg = DG2D(nx, ny, box, k, basis, ph, obc)
+    return solver, dg
+
+
+def make_pair_1d(nx, box, k, physics, tab, bcs, precision, gamma=1.4, beta=1.0):
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    codes = [gpu_bc(bcs[0]), gpu_bc(bcs[1])]
+    mesh = B.make_mesh(1, nx, 1, box, [codes[0][0], codes[1][0], 0, 0], [codes[0][1], codes[1][1], 0, 0],
+                       [codes[0][2], codes[1][2], None, None])
+    phys_id = B.EULER if physics == "euler" else B.ADVECTION
+    solver = B.Solver(mesh, k, B.BASIS_P, GTB.BY_NAME[tab], phys_id, B.F64 if precision == "f64" else B.F32,
+                      gamma=gamma, beta=(beta, 0.0))
+    ph = Euler(gamma, 1) if physics == "euler" else Advection([beta])
+
+    def obc1(d):
+        if d[0] in ("periodic", "outflow"):
+            return d[0]
+        if d[0] == "const":
+            st = np.asarray(d[1], dtype=np.float64)
+            return ("dirichlet", lambda t: st)
+        if d[0] == "sine":
+            A, kx, ky, w, phs = d[1:]
+            x = box[0]
+            return ("dirichlet", lambda t: np.array([A * np.sin(kx * x - w * t + phs)]))
+        raise ValueError(d)
+    dg = DG1D(np.linspace(box[0], box[1], nx + 1), k, ph, bc=(obc1(bcs[0]), obc1(bcs[1])))
+    return solver, dg
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))

@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle
+on identical seeded inputs.
+
+Tolerances: FP64 builds agree with the oracle to 1e-13 relative after one
+step and 1e-12 after several (summation order differs); FP32 builds to
+2e-5 relative after one step (FP32 rounding of O(1e3) operations per value).
+Meshes span several 30-column warp strips and several row segments, with a
+ragged tail in both directions."""
+import numpy as np
+import pytest
+
+import crkdg_inputs as inp
+from oracle import tableaux as OTB
+from oracle.dg1d import crkdg_step as ocrkdg1
+from oracle.dg2d import cfl_dt_2d, crkdg_step as ocrkdg2
+from oracle.limiter import tvb_limit
+from tests.pairing import TAB_NAMES, from_planes, make_pair_1d, make_pair_2d, rel_err, to_planes
+
+pytestmark = pytest.mark.gpu
+
+PER = {s: ("periodic",) for s in "WESN"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_06471_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("k,basis,tab", [(1, "P", "midpoint"), (2, "P", "heun3"), (2, "P", "ssprk3"),
+                                         (2, "Q", "rk4"), (3, "P", "rk4"), (3, "Q", "rk4"), (1, "Q", "heun2"),
+                                         (0, "P", "ssprk3")])
+def test_one_step_euler_f64(k, basis, tab):
+    nx, ny = 67, 23
+    gs, dg = make_pair_2d(nx, ny, (0, 1.3, 0, 0.9), k, basis, "euler", tab, PER, "f64")
+    gs.set_launch(seg_rows=8)
+    u = inp.random_modal_state(ny, nx, k, basis, "euler", seed=100 + k)
+    gs.set_state(to_planes(u), 0.0)
+    dt = 0.2 * cfl_dt_2d(dg, u, 1.0)
+    gs.step(dt)
+    got = from_planes(gs.get_state())
+    want = ocrkdg2(dg, u, 0.0, dt, TAB_NAMES[tab])
+    assert rel_err(got, want) < 1e-13
+    code, st = gs.sync()
+    assert code == 0 and st == 0
+
+
+@pytest.mark.parametrize("k,basis,tab", [(2, "P", "ssprk3"), (2, "Q", "rk4"), (1, "P", "midpoint")])
+def test_one_step_euler_f32(k, basis, tab):
+    nx, ny = 61, 37
+    gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), k, basis, "euler", tab, PER, "f32")
+    gs.set_launch(seg_rows=12)
+    u = inp.random_modal_state(ny, nx, k, basis, "euler", seed=7)
+    u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))   # representable input
+    gs.set_state(to_planes(u), 0.0)
+    dt = 0.2 * cfl_dt_2d(dg, u, 1.0)
+    gs.step(dt)
+    got = from_planes(gs.get_state())
+    want = ocrkdg2(dg, u, 0.0, dt, TAB_NAMES[tab])
+    assert rel_err(got, want) < 2e-5
+
+
+def test_ten_steps_euler_f64_and_conservation():
+    nx, ny = 45, 31
+    gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), 2, "P", "euler", "ssprk3", PER, "f64")
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=3)
+    gs.set_state(to_planes(u), 0.0)
+    w = u.copy()
+    t = 0.0
+    for _ in range(10):
+        dt = gs.cfl_dt(0.15)
+        assert dt == pytest.approx(cfl_dt_2d(dg, w, 0.15), rel=1e-13)
+        gs.step(dt)
+        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3)
+        t += dt
+    got = from_planes(gs.get_state())
+    assert rel_err(got, w) < 1e-12
+    sums = gs.conservation()
+    assert np.allclose(sums, dg.total(w), rtol=1e-13)
+    assert np.allclose(sums, dg.total(u), rtol=1e-13)
+    assert gs.time() == pytest.approx(t)
+
+
+@pytest.mark.parametrize("k,basis", [(3, "P"), (2, "Q"), (1, "P")])
+def test_advection_with_inflow_boundaries_f64(k, basis):
+    """Linear advection with time-dependent inflow data on W and S and
+    outflow on E and N: boundary data at t^n + c_i dt in the final stage."""
+    bcs = {"W": ("sine_prod", 1.0, np.pi, 1.0, np.pi, 0.5), "S": ("sine_prod", 1.0, np.pi, 1.0, np.pi, 0.5),
+           "E": ("outflow",), "N": ("outflow",)}
+    nx, ny = 40, 33
+    gs, dg = make_pair_2d(nx, ny, (-1, 1, -1, 1), k, basis, "advection", "rk4", bcs, "f64", beta=(1.0, 0.5))
+    gs.set_launch(seg_rows=10)
+    u = inp.random_modal_state(ny, nx, k, basis, "advection", seed=11)
+    gs.set_state(to_planes(u), 0.3)
+    w = u.copy()
+    t = 0.3
+    for _ in range(3):
+        gs.step(0.01)
+        w = ocrkdg2(dg, w, t, 0.01, OTB.RK4)
+        t += 0.01
+    assert rel_err(from_planes(gs.get_state()), w) < 1e-12
+
+
+def _dmr_bcs():
+    st = inp.dmr_states()
+    post, pre = list(st["post"]), list(st["pre"])
+    return {"W": ("const", post), "E": ("outflow",), "S": ("dmr_bottom", post, st["x0"]),
+            "N": ("dmr_top", post, pre, st["x0"], st["slope"], st["xspeed"])}, st
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
+def test_dmr_boundaries_and_limiter(prec, tol):
+    """Double Mach reflection set-up: inflow W, outflow E, wall + post-shock
+    S, exact shock motion N; TVB limiter M = 50 at the end of each step
+    (applied on load by the next step, and by get_state)."""
+    bcs, st = _dmr_bcs()
+    nx, ny = 64, 17
+    gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, prec)
+    gs.set_launch(seg_rows=6)
+    X, Y = dg.volume_points()
+    u = dg.project(lambda X, Y: inp.dmr_ic(X, Y, st))
+    if prec == "f32":
+        u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
+    gs.set_state(to_planes(u), 0.0)
+    gs.limit(50.0)
+    w = tvb_limit(dg, u, 50.0, 0.0)[0]
+    t = 0.0
+    for _ in range(3):
+        dt = gs.cfl_dt(0.16)
+        gs.step(dt)
+        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3, limiter=lambda v, tt: tvb_limit(dg, v, 50.0, tt)[0])
+        t += dt
+    got = from_planes(gs.get_state())
+    assert rel_err(got, w) < tol
+    assert gs.troubled_count() > 0
+
+
+def test_limiter_alone_matches_oracle_flags():
+    nx, ny = 50, 40
+    gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f64")
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=21, amp=0.6)
+    gs.set_state(to_planes(u), 0.0)
+    gs.limit(5.0)
+    got = from_planes(gs.get_state())
+    want, flags = tvb_limit(dg, u, 5.0, 0.0)
+    assert flags.any() and not flags.all()
+    assert rel_err(got, want) < 1e-13
+
+
+def test_graph_capture_equals_eager_and_launch_shapes_agree():
+    import torch
+    nx, ny = 95, 70
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=5)
+    outs = []
+    stream = torch.cuda.Stream()
+    for (L, w, cap) in [(8, 4, False), (16, 2, True), (5, 1, True), (70, 8, False)]:
+        gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f32")
+        gs.close()
+        from paper_2307_06471_gb300 import binding as B
+        from paper_2307_06471_gb300 import tableaux as GTB
+        g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32, stream=stream.cuda_stream)
+        g.set_launch(L, w)
+        g.set_state(to_planes(u), 0.0)
+        g.advance(6, 0.2, 1.0, capture=cap)
+        g.advance(6, 0.2, 1.0, capture=cap)
+        outs.append(g.get_state())
+        t = g.time()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    assert t > 0
+
+
+def test_stencil_is_five_points_on_gpu():
+    nx, ny = 40, 36
+    gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "rk4", PER, "f64")
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=9)
+    v = u.copy()
+    c = (17, 29)
+    v[c] += 1e-3 * np.abs(u[c])
+    res = []
+    for s in (u, v):
+        gs.set_state(to_planes(s), 0.0)
+        gs.step(1e-3)
+        res.append(gs.get_state())
+    ch = {tuple(p) for p in np.argwhere(np.any(res[0] != res[1], axis=(0, 1)))}
+    y, x = c
+    assert ch == {(y, x), (y - 1, x), (y + 1, x), (y, x - 1), (y, x + 1)}
+
+
+@pytest.mark.parametrize("k,tab", [(2, "heun3"), (1, "midpoint"), (3, "rk4")])
+def test_1d_advection_inflow_f64(k, tab):
+    """Table 4.4 set-up (u_t + u_x = 0, inflow sin(-t) at x = 0) for a few steps."""
+    N = 97
+    gs, dg = make_pair_1d(N, (0, 4 * np.pi), k, "advection", tab, (("sine", 1.0, 1.0, 0.0, 1.0, 0.0), ("outflow",)),
+                          "f64")
+    u0 = dg.project(lambda x: np.sin(x)[..., None])
+    gs.set_state(to_planes(u0), 0.0)
+    dt = 0.16 * 4 * np.pi / N
+    w = u0.copy()
+    t = 0.0
+    for _ in range(5):
+        gs.step(dt)
+        w = ocrkdg1(dg, w, t, dt, TAB_NAMES[tab])
+        t += dt
+    assert rel_err(from_planes(gs.get_state(), 1), w) < 1e-12
+
+
+def test_1d_persistent_run_matches_stepping():
+    """Config-1 path: 160 cells, P^2, SSP-RK3, dt = 2 pi / 1600, whole run
+    in one launch == step by step == oracle (sampled at 40 steps)."""
+    N = 160
+    gs, dg = make_pair_1d(N, (0, 2 * np.pi), 2, "advection", "ssprk3", (("periodic",), ("periodic",)), "f64")
+    u0 = dg.project(lambda x: np.sin(x)[..., None])
+    dt = 2 * np.pi / 1600
+    gs.set_state(to_planes(u0), 0.0)
+    gs.run_fixed(40, dt)
+    a = gs.get_state()
+    gs.set_state(to_planes(u0), 0.0)
+    for _ in range(40):
+        gs.step(dt)
+    b = gs.get_state()
+    assert np.array_equal(a, b)
+    w = u0.copy()
+    for n in range(40):
+        w = ocrkdg1(dg, w, n * dt, dt, OTB.SSPRK3)
+    assert rel_err(from_planes(a, 1), w) < 1e-12
+
+
+def test_1d_euler_f64():
+    N = 75
+    gs, dg = make_pair_1d(N, (0, 2), 2, "euler", "heun3", (("periodic",), ("periodic",)), "f64")
+    u = inp.random_modal_state_1d(N, 2, 3, seed=4)
+    gs.set_state(to_planes(u), 0.0)
+    w = u.copy()
+    for n in range(4):
+        gs.step(0.002)
+        w = ocrkdg1(dg, w, n * 0.002, 0.002, OTB.HEUN3)
+    assert rel_err(from_planes(gs.get_state(), 1), w) < 1e-12
+
+
+def test_project_ic_matches_oracle_projection():
+    nx, ny = 33, 21
+    gs, dg = make_pair_2d(nx, ny, (0, 10, 0, 10), 2, "Q", "euler", "rk4", PER, "f64")
+    gs.project_function(lambda X, Y: inp.vortex_ic(X, Y))
+    X, Y = dg.volume_points()
+    vals = inp.vortex_ic(X, Y)
+    want = dg.project_point_values(vals)
+    assert rel_err(from_planes(gs.get_state()), want) < 1e-13
+
+
+def test_errors_are_reported_not_trapped():
+    from paper_2307_06471_gb300 import binding as B
+    nx, ny = 31, 9
+    gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 1, "P", "euler", "midpoint", PER, "f64")
+    u = inp.random_modal_state(ny, nx, 1, "P", "euler", seed=1)
+    u[4, 5, 0, 0] = -1.0          # negative density in one cell, uploaded from the host
+    gs.set_state(to_planes(u), 0.0)
+    gs.step(1e-4)
+    code, st = gs.sync()
+    assert code == B.ENONPHYSICAL and st & B.ST_NONPHYSICAL
+    code, st = gs.sync()           # status is cleared after reading
+    assert code == 0
+    with pytest.raises(B.CrkdgError):
+        gs.step(-1.0)
