@@ -11,7 +11,8 @@ The Lax--Friedrichs flux of Sec. 2.1 is
 For linear advection alpha = |beta . nu| and fhat is the upwind flux
 (Remark 3.5 / Sec. 4.1.1).  For Euler the paper uses the *local* LF flux;
 the reading taken here: alpha is evaluated per face quadrature point and per
-RK stage as max(|vel.nu| + c) over the two traces.
+RK stage as max(|vel.nu| + c) over the two traces, with c = 0 where
+gamma p / rho < 0 (alpha is undefined for such non-hyperbolic point values).
 
 Arrays carry the variable index last: u[..., v].  Test infrastructure only.
 """
@@ -75,12 +76,16 @@ class Euler:
         return out
 
     def sound(self, u):
+        """c = sqrt(gamma p / rho); a state with gamma p / rho < 0 (a point
+        value past a strong shock) is not hyperbolic and d f / d u has no
+        real eigenvalues there: the reading taken is c = 0."""
         rho, vel, p = self.primitive(u)
-        return np.sqrt(self.gamma * p / rho)
+        return np.sqrt(np.maximum(self.gamma * p / rho, 0.0))
 
     def speed(self, u, axis):
+        """|vel . nu| + c, the spectral radius of d f / d u . nu (LF alpha)."""
         rho, vel, p = self.primitive(u)
-        return np.abs(vel[axis]) + np.sqrt(self.gamma * p / rho)
+        return np.abs(vel[axis]) + self.sound(u)
 
     def conserved(self, rho, vel, p):
         """Conserved state from primitive (rho, [w, v], p); trailing axis = variable."""
