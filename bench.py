@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Throughput of the compact RKDG (cRKDG) time step on GB300.
+
+Workload (one GPU): the double Mach reflection of the paper's Sec. 4.2.2 --
+2D Euler (gamma = 1.4), Mach 10 shock at 60 degrees, [0,4] x [0,1],
+1920 x 480 cells, P^2 (24 DOF per cell), SSP-RK3 in Butcher form, TVB-minmod
+limiter M = 50 once per step followed by the positivity-preserving scaling
+(Zhang--Shu; needed at Mach 10), FP32 bulk with FP64 CFL / conservation
+reductions, CFL 0.16.  Synthetic: the analytic initial data, advanced W
+warm-up steps before timing.
+
+A "step" is one full cRKDG time step (limit-on-load, all inner stages, the
+final DG stage with boundary data, the FP64 reductions that give the next
+dt) -- one launch of the fused step kernel with dt read on the device.
+
+value  : DOF-updates/s = cells * 24 * K / (sum of per-step device times),
+         CUDA events on the solver's stream around each step, L2 flushed
+         (256 MiB write) between timed steps, outside the events.
+e2e    : the same metric through the C ABI with host buffers: upload of the
+         FP64 initial state from host memory, K x (crkdg_cfl_dt -> host,
+         crkdg_step(dt)), download of the FP64 state; wall clock.
+--impl reference : the FP64 CPU oracle (numpy) on a bounded sample of the
+         same workload (a 240 x 60 mesh of the same problem), timed on the
+         host cores; rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WL = dict(name="dmr_1920x480_P2_ssprk3_tvb50_f32", nx=1920, ny=480, k=2, basis="P", tab="ssprk3", M=50.0,
+          pp_eps=1e-10, cfl=0.16, T=0.2, box=(0.0, 4.0, 0.0, 1.0))
+METRIC = "2D Euler P2 cRKDG DOF-updates/s"
+UNIT = "DOF-updates/s"
+SAMPLE = dict(nx=240, ny=60)      # bounded oracle sample of the same problem
+
+# ncu dram traffic of the step kernel for this workload, per launch, and the
+# hash of the kernel sources it was taken with (None until captured)
+TRAFFIC = {"bytes": None, "src_hash": None}
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("step2d.cuh", "common.cuh", "limiter.cuh", "tables.cuh"):
+        with open(os.path.join(ROOT, "paper_2307_06471_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dmr_mesh(B, inp, nx, ny):
+    st = inp.dmr_states()
+    post, pre = list(st["post"]), list(st["pre"])
+    bc = [B.BC_DIRICHLET, B.BC_OUTFLOW, B.BC_DIRICHLET, B.BC_DIRICHLET]
+    fn = [B.FN_CONST, 0, B.FN_DMR_BOTTOM, B.FN_DMR_TOP]
+    params = [post, None, post + [st["x0"]], post + pre + [st["x0"], st["slope"], st["xspeed"]]]
+    return B.make_mesh(2, nx, ny, WL["box"], bc, fn, params), st
+
+
+def make_solver(stream_handle, nx, ny):
+    import crkdg_inputs as inp
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    mesh, st = dmr_mesh(B, inp, nx, ny)
+    s = B.Solver(mesh, WL["k"], B.BASIS_P, GTB.BY_NAME[WL["tab"]], B.EULER, B.F32, stream=stream_handle)
+    s.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    s.limit(WL["M"])
+    s.positivity(WL["pp_eps"])
+    return s
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_sample(nx, ny, steps, warm=1):
+    """Run the FP64 oracle on the bounded sample in a single-threaded child
+    process; returns (DOF-updates/s, seconds, steps)."""
+    code = r"""
+import json, sys, time, os
+sys.path.insert(0, %r)
+import numpy as np
+import crkdg_inputs as inp
+from oracle import tableaux as TB
+from oracle.dg2d import DG2D, crkdg_step, cfl_dt_2d
+from oracle.limiter import tvb_limit, positivity_limit
+from oracle.physics import Euler
+nx, ny, steps, warm = %d, %d, %d, %d
+st = inp.dmr_states()
+post, pre = st['post'], st['pre']
+def refl(u, axis):
+    o = np.array(u, copy=True); o[..., 1 + axis] = -o[..., 1 + axis]; return o
+bc = {'W': ('dirichlet', lambda X, Y, t: np.broadcast_to(post, np.shape(X) + (4,)).copy()), 'E': 'outflow',
+      'S': ('custom', lambda u, X, Y, t: np.where((np.asarray(X) < st['x0'])[..., None], post, refl(u, 1))),
+      'N': ('dirichlet', lambda X, Y, t: np.where((np.asarray(X) < st['x0'] + st['slope'] * np.asarray(Y) + st['xspeed'] * t)[..., None], post, pre))}
+dg = DG2D(nx, ny, (0, 4, 0, 1), 2, 'P', Euler(1.4, 2), bc)
+u = dg.project(lambda X, Y: inp.dmr_ic(X, Y, st), nq=3)
+lim = lambda v, t: positivity_limit(dg, tvb_limit(dg, v, 50.0, t)[0], 1e-10)
+u = lim(u, 0.0)
+t = 0.0
+for i in range(warm + steps):
+    if i == warm:
+        t0 = time.perf_counter()
+    dt = cfl_dt_2d(dg, u, 0.16)
+    u = crkdg_step(dg, u, t, dt, TB.SSPRK3, limiter=lim)
+    t += dt
+el = time.perf_counter() - t0
+print(json.dumps({'sec': el, 'steps': steps, 'dofs': nx * ny * 24}))
+""" % (ROOT, nx, ny, steps, warm)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["dofs"] * d["steps"] / d["sec"], d["sec"], d["steps"]
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    return rank, ws
+
+
+def run_reference(args):
+    rank, ws = dist_init()
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    # bound the run to a few minutes: ~1.3 s per oracle step at 240 x 60
+    nx, ny = SAMPLE["nx"], SAMPLE["ny"]
+    if steps > 60:
+        nx, ny = 120, 30
+    rate, sec, n = oracle_sample(nx, ny, steps, warm=max(1, min(args.warmup, 3)))
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL["name"], "sample_mesh": "%dx%d" % (nx, ny), "k": 2, "basis": "P",
+                       "tableau": "ssprk3", "limiter": "tvb M=50"},
+            "impl": "reference",
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB, %d steps, 1 thread (%s)"
+                                       % (nx, ny, n, cpu_model())},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import numpy as np
+    import torch
+
+    rank, ws = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300.workcount import step_bytes_per_cell, step_flops_per_cell
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+
+    nx, ny = WL["nx"], WL["ny"]
+    cells = nx * ny
+    dof = cells * 24
+    stream = torch.cuda.Stream()
+    s = make_solver(stream.cuda_stream, nx, ny)
+    if args.autotune:
+        s.autotune()
+    seg_rows, wpb = s.get_launch()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up: device-driven steps (first dt from a reduction of the state)
+    s.advance(args.warmup, WL["cfl"], WL["T"])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            starts[i].record(stream)
+            s.step_device()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    code, status = s.sync()
+    t_sim = s.time()
+    ms = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
+    dev_ms = float(ms.item())
+    ms_per_step = dev_ms / args.steps
+    value = ws * dof * args.steps / (dev_ms * 1e-3)
+
+    A, b = GTB.BY_NAME[WL["tab"]]
+    fpc = step_flops_per_cell(WL["k"], WL["basis"], "euler", A, b, limiter=True)
+    bpc = step_bytes_per_cell(WL["k"], WL["basis"], "euler", 4)
+    clocks = clk.summary()
+    peaks, peak_kind = measured_peaks()
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    achieved = fpc * cells / (ms_per_step * 1e-3) / 1e12
+    hbm = bpc * cells / (ms_per_step * 1e-3) / 1e9
+    traffic = TRAFFIC["bytes"] if TRAFFIC["src_hash"] == kernel_src_hash() else None
+
+    e2e = None
+    if not args.no_e2e:
+        import crkdg_inputs as inp  # noqa: F401
+        s2 = make_solver(None, nx, ny)
+        s2.advance(args.warmup, WL["cfl"], WL["T"])
+        host = s2.get_state()                      # FP64 host state (input of the timed run)
+        out = np.empty_like(host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.set_state(host, 0.0)
+        s2.limit(WL["M"])
+        s2.positivity(WL["pp_eps"])
+        for _ in range(args.steps):
+            dt = s2.cfl_dt(WL["cfl"])
+            s2.step(dt)
+        out[...] = s2.get_state()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e = {"value": ws * dof * args.steps / wall, "unit": UNIT,
+               "h2d_bytes_per_step": (host.nbytes // 2) // args.steps,
+               "d2h_bytes_per_step": 8 + (out.nbytes // 2) // args.steps,
+               "note": "FP64 host state converted to FP32 and uploaded once, dt read back every step, "
+                       "state downloaded once; bytes counted as transferred (FP32 on the link)"}
+        s2.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, sec, n = oracle_sample(SAMPLE["nx"], SAMPLE["ny"], 8)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB, %d steps (%.1f s), 1 thread, %s"
+                         % (SAMPLE["nx"], SAMPLE["ny"], n, sec, cpu_model())}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WL["name"], "cells": cells, "dof_per_cell": 24, "k": 2, "basis": "P",
+                           "tableau": "ssprk3", "limiter": "tvb M=50 + positivity scaling (once per step)", "cfl": WL["cfl"],
+                           "reductions": "fp64", "l2": "flushed (256 MiB) between timed steps",
+                           "launch": {"seg_rows": seg_rows, "warps_per_block": wpb},
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": achieved / fp32_peak, "traffic": traffic,
+                             "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (%s max clock)"
+                                          % (mhz, peak_kind),
+                             "flop_per_cell": fpc, "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / peaks["hbm_gbs"]},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+                "status": {"code": code, "bits": status, "t_sim": t_sim},
+                "cpu_baseline": cpu}
+        print(json.dumps(line))
+    s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -158,6 +158,20 @@ int crkdg_advance(crkdg_ctx* ctx, int n_steps, double cfl, double t_end, int cap
  * pending limit of an earlier step is still applied). */
 int crkdg_limit(crkdg_ctx* ctx, double M_tvb);
 
+/* Positivity-preserving scaling (Zhang and Shu, J. Comput. Phys. 229, 2010;
+ * not part of the paper's method).  eps > 0: after the TVB limiter (if on)
+ * at the end of every following step, scale each cell's non-constant modes
+ * so that density and pressure are >= eps at the volume and face Gauss
+ * points; cell averages are unchanged.  Marks the current state pending like
+ * crkdg_limit.  eps <= 0: off.  2D Euler only (CRKDG_EUNSUPPORTED otherwise). */
+int crkdg_positivity(crkdg_ctx* ctx, double eps);
+
+/* One step with dt taken from the device run state: the dt that the fused
+ * reduction of the previous step (or of crkdg_advance's first reduction)
+ * computed, dt = min(cfl / maxspeed, t_end - t) with the cfl and t_end of the
+ * last crkdg_advance.  No host synchronisation (2D only). */
+int crkdg_step_device(crkdg_ctx* ctx);
+
 /* Fixed-dt run of n_steps steps.  1D meshes of up to 960 cells run the whole
  * sequence in one single-block launch (block barrier between steps). */
 int crkdg_run_fixed(crkdg_ctx* ctx, int n_steps, double dt);

@@ -57,7 +57,9 @@ _SIGS = {
     "crkdg_step": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_advance": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "crkdg_run_fixed": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "crkdg_step_device": (C.c_int, [C.c_void_p]),
     "crkdg_limit": (C.c_int, [C.c_void_p, C.c_double]),
+    "crkdg_positivity": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_conservation": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_troubled_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
     "crkdg_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint)]),
@@ -191,11 +193,17 @@ class Solver:
     def advance(self, n_steps, cfl, t_end, capture=False):
         _check(lib().crkdg_advance(self.ctx, int(n_steps), float(cfl), float(t_end), 1 if capture else 0))
 
+    def step_device(self):
+        _check(lib().crkdg_step_device(self.ctx))
+
     def run_fixed(self, n_steps, dt):
         _check(lib().crkdg_run_fixed(self.ctx, int(n_steps), float(dt)))
 
     def limit(self, M):
         _check(lib().crkdg_limit(self.ctx, float(M)))
+
+    def positivity(self, eps):
+        _check(lib().crkdg_positivity(self.ctx, float(eps)))
 
     def conservation(self):
         s = np.empty(self.n_vars)

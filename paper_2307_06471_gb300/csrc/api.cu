@@ -64,6 +64,8 @@ struct crkdg_ctx {
     double M;
     bool pending;
     double M_pending;
+    double pp_eps;        // positivity floor for following steps (0: off)
+    double pp_pending;    // positivity floor of the pending limit
     int seg_rows, wpb;
     int kphys;   // kernel physics id
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -153,6 +155,7 @@ int enqueue_reduce(crkdg_ctx* c, int set_dt) {
 int enqueue_limit(crkdg_ctx* c, double M) {
     StepArgs a = base_args(c);
     a.M = M;
+    a.pp_eps = c->pp_pending;
     a.t = c->t;
     CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, c->u[c->cur], c->d_flags, c->stream));
     return CRKDG_OK;
@@ -168,6 +171,7 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
     a.dt_from_dev = dt_from_dev;
     a.limit = limit;
     a.M = M;
+    a.pp_eps = limit ? c->pp_pending : 0.0;
     if (c->dim == 2) {
         int ns, nseg;
         strips_segs(c, c->seg_rows, &ns, &nseg);
@@ -432,8 +436,9 @@ int crkdg_step(crkdg_ctx* c, double dt) {
     int r = enqueue_step(c, dt, 0, lim, lim ? c->M_pending : 0.0);
     if (r) return r;
     c->t += dt;
-    c->pending = c->limiter_on && c->dim == 2;
+    c->pending = (c->limiter_on || c->pp_eps > 0.0) && c->dim == 2;
     c->M_pending = c->M;
+    c->pp_pending = c->pp_eps;
     return CRKDG_OK;
 }
 
@@ -449,8 +454,9 @@ int crkdg_advance(crkdg_ctx* c, int n_steps, double cfl, double t_end, int captu
     int r = enqueue_reduce(c, 1);
     if (r) return r;
     const int lim_first = c->pending ? 1 : 0;
-    const int lim_rest = c->limiter_on ? 1 : 0;
+    const int lim_rest = (c->limiter_on || c->pp_eps > 0.0) ? 1 : 0;
     const double M_first = c->M_pending, M_rest = c->M;
+    const double pp_first = c->pp_pending, pp_rest = c->pp_eps;
     int ns, nseg;
     strips_segs(c, c->seg_rows, &ns, &nseg);
     r = ensure_partials(c, (size_t)ns * nseg * 8);
@@ -458,6 +464,7 @@ int crkdg_advance(crkdg_ctx* c, int n_steps, double cfl, double t_end, int captu
     auto enqueue_all = [&]() -> int {
         for (int i = 0; i < n_steps; ++i) {
             const int lim = i == 0 ? lim_first : lim_rest;
+            c->pp_pending = i == 0 ? pp_first : pp_rest;
             int rr = enqueue_step(c, 0.0, 1, lim, i == 0 ? M_first : M_rest);
             if (rr) return rr;
         }
@@ -489,8 +496,22 @@ int crkdg_advance(crkdg_ctx* c, int n_steps, double cfl, double t_end, int captu
         if (n_steps % 2) c->cur ^= 1;
     }
     c->t_known = false;
-    c->pending = c->limiter_on;
+    c->pending = c->limiter_on || c->pp_eps > 0.0;
     c->M_pending = c->M;
+    c->pp_pending = c->pp_eps;
+    return CRKDG_OK;
+}
+
+int crkdg_step_device(crkdg_ctx* c) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "crkdg_step_device is 2D only");
+    const int lim = c->pending ? 1 : 0;
+    int r = enqueue_step(c, 0.0, 1, lim, c->M_pending);
+    if (r) return r;
+    c->t_known = false;
+    c->pending = c->limiter_on || c->pp_eps > 0.0;
+    c->M_pending = c->M;
+    c->pp_pending = c->pp_eps;
     return CRKDG_OK;
 }
 
@@ -533,9 +554,27 @@ int crkdg_limit(crkdg_ctx* c, double M) {
         c->M = M;
         c->pending = true;
         c->M_pending = M;
+        c->pp_pending = c->pp_eps;
     } else {
         c->limiter_on = false;
         c->M = -1.0;
+    }
+    return CRKDG_OK;
+}
+
+int crkdg_positivity(crkdg_ctx* c, double eps) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2 || c->physics != CRKDG_EULER)
+        return fail(CRKDG_EUNSUPPORTED, "positivity scaling is built for 2D Euler");
+    if (eps > 0.0) {
+        c->pp_eps = eps;
+        if (!c->pending) {
+            c->pending = true;
+            c->M_pending = -1.0;
+        }
+        c->pp_pending = eps;
+    } else {
+        c->pp_eps = 0.0;
     }
     return CRKDG_OK;
 }
@@ -683,7 +722,7 @@ int crkdg_save(crkdg_ctx* c, const char* path) {
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(CRKDG_EINVAL, std::string("cannot open ") + path);
     const int hdr[8] = {0x43524b44, 1, c->dim, c->mesh.nx, c->mesh.ny, c->nv, c->nm, c->precision};
-    const double dh[4] = {t, pend ? 1.0 : 0.0, Mp, c->limiter_on ? c->M : -1.0};
+    const double dh[6] = {t, pend ? 1.0 : 0.0, Mp, c->limiter_on ? c->M : -1.0, c->pp_pending, c->pp_eps};
     bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(dh, sizeof(dh), 1, f) == 1 &&
               std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size();
     ok = (std::fclose(f) == 0) && ok;
@@ -695,7 +734,7 @@ int crkdg_load(crkdg_ctx* c, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(CRKDG_EINVAL, std::string("cannot open ") + path);
     int hdr[8];
-    double dh[4];
+    double dh[6];
     std::vector<double> h(c->elems);
     bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(dh, sizeof(dh), 1, f) == 1;
     ok = ok && hdr[0] == 0x43524b44 && hdr[2] == c->dim && hdr[3] == c->mesh.nx && hdr[4] == c->mesh.ny &&
@@ -709,6 +748,8 @@ int crkdg_load(crkdg_ctx* c, const char* path) {
     c->M_pending = dh[2];
     c->limiter_on = dh[3] >= 0.0;
     c->M = dh[3];
+    c->pp_pending = dh[4];
+    c->pp_eps = dh[5];
     return CRKDG_OK;
 }
 

@@ -171,9 +171,12 @@ __global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned lon
                 for (int v = 0; v < NV; ++v) nb[s][v] = u[(size_t)(v * NM) * plane + (size_t)cy * nx + cx];
             }
         }
-        fl = tvb_limit_cell<T, NV, NM>(c, nb[0], nb[1], nb[2], nb[3], T(a.M * a.dx * a.dx), T(a.M * a.dy * a.dy),
-                                       T(a.gamma));
-        if (fl)
+        if (a.M >= 0.0)
+            fl = tvb_limit_cell<T, NV, NM>(c, nb[0], nb[1], nb[2], nb[3], T(a.M * a.dx * a.dx),
+                                           T(a.M * a.dy * a.dy), T(a.gamma));
+        bool sc = false;
+        if (a.pp_eps > 0.0) sc = positivity_cell<T, NV, NM, K, B>(c, T(a.gamma), T(a.pp_eps));
+        if (fl || sc)
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll

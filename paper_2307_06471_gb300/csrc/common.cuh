@@ -46,8 +46,9 @@ struct StepArgs {
     const double* tab;        // device: a[MAXS*MAXS] row-major, b[MAXS], c[MAXS]
     BCSide bc[4];             // W, E, S, N
     int seg_len, n_strips, n_segs;
-    int limit;                // 1: limit u^n on load with TVB parameter M
-    double M;
+    int limit;                // 1: limit u^n on load (final-stage limiters of the previous step)
+    double M;                 // TVB parameter; < 0: no TVB limiter
+    double pp_eps;            // > 0: positivity-preserving scaling with this floor
     double gamma;
     double beta[2];
 };

@@ -165,3 +165,92 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
 }
 
 }  // namespace crk
+
+namespace crk {
+
+// Positivity-preserving scaling of Zhang and Shu (J. Comput. Phys. 229,
+// 2010) -- an option outside the paper's method, applied after the TVB
+// limiter at the same final stage.  Points: the volume Gauss points and the
+// Gauss points of the four faces.  Step 1 scales the density's non-constant
+// modes so that rho >= eps at every point; step 2 scales every non-constant
+// mode by the smallest t in (0, 1] with p(ubar + t (u_q - ubar)) = eps over
+// the points where p(u_q) < eps (a quadratic in t after multiplying by rho).
+// The cell average is unchanged.  Returns true if the cell was scaled.
+template <class T, int NV, int NM, int K, int B>
+__device__ __forceinline__ bool positivity_cell(T (&u)[NV][NM], T gamma, T eps) {
+    if constexpr (NV != 4 || NM < 2) {
+        return false;
+    } else {
+        constexpr Tab2D<K, B> tb = make_tab2d<K, B>();
+        constexpr int NQ = K + 1, NQV = NQ * NQ, NPT = NQV + 4 * NQ;
+        auto phi = [&](int q, int m) -> T {
+            if (q < NQV) return T(tb.phi[q][m]);
+            const int f = (q - NQV) / NQ, p = (q - NQV) % NQ;
+            return T(f == 0 ? tb.tE[p][m] : f == 1 ? tb.tW[p][m] : f == 2 ? tb.tN[p][m] : tb.tS[p][m]);
+        };
+        bool changed = false;
+        // step 1: density
+        const T rbar = u[0][0];
+        T rmin = rbar;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            T r = T(0);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) r += u[0][m] * phi(q, m);
+            rmin = r < rmin ? r : rmin;
+        }
+        if (rmin < eps) {
+            T den = rbar - rmin;
+            T th = den > T(0) ? (rbar - eps) / den : T(0);
+            th = th < T(1) ? (th > T(0) ? th : T(0)) : T(1);
+#pragma unroll
+            for (int m = 1; m < NM; ++m) u[0][m] *= th;
+            changed = true;
+        }
+        // step 2: pressure
+        const T kk = eps / (gamma - T(1));
+        const T rb = u[0][0], mxb = u[1][0], myb = u[2][0], eb = u[3][0];
+        const T c = rb * eb - T(0.5) * (mxb * mxb + myb * myb) - kk * rb;
+        T th2 = T(1);
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            T d[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T s = T(0);
+#pragma unroll
+                for (int m = 1; m < NM; ++m) s += u[v][m] * phi(q, m);
+                s += u[v][0] * phi(q, 0) - u[v][0];
+                d[v] = s;
+            }
+            const T a = d[0] * d[3] - T(0.5) * (d[1] * d[1] + d[2] * d[2]);
+            const T b = rb * d[3] + eb * d[0] - (mxb * d[1] + myb * d[2]) - kk * d[0];
+            if (a + b + c < T(0)) {
+                T disc = b * b - T(4) * a * c;
+                disc = sqrt(disc > T(0) ? disc : T(0));
+                const T qq = T(-0.5) * (b + (b >= T(0) ? disc : -disc));
+                T r = T(1e30);
+                if (qq != T(0)) {
+                    const T r1 = c / qq;
+                    if (r1 > T(0) && r1 <= T(1)) r = r1;
+                }
+                if (a != T(0)) {
+                    const T r2 = qq / a;
+                    if (r2 > T(0) && r2 <= T(1) && r2 < r) r = r2;
+                }
+                if (r > T(1)) r = T(0);
+                th2 = r < th2 ? r : th2;
+            }
+        }
+        if (th2 < T(1)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 1; m < NM; ++m) u[v][m] *= th2;
+            changed = true;
+        }
+        return changed;
+    }
+}
+
+}  // namespace crk

@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
             if (!perx && col == nx - 1) load_avg_x(nx, ry_, nbE);
             const bool real = perx ? true : (col >= 0 && col < nx);
             bool fl = false;
-            if (real) fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam);
+            if (real && a.M >= 0.0) fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam);
+            if (real && a.pp_eps > 0.0) positivity_cell<T, NV, NM, K, B>(un, gam, T(a.pp_eps));
             if (out_row && outlane && fl) ++red_trouble;
 #pragma unroll
             for (int v = 0; v < NV; ++v) avg_prev[v] = avg_cur[v];

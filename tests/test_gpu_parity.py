@@ -111,8 +111,10 @@ def _dmr_bcs():
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
 def test_dmr_boundaries_and_limiter(prec, tol):
     """Double Mach reflection set-up: inflow W, outflow E, wall + post-shock
-    S, exact shock motion N; TVB limiter M = 50 at the end of each step
-    (applied on load by the next step, and by get_state)."""
+    S, exact shock motion N; TVB limiter M = 50 followed by the positivity
+    scaling at the end of each step (applied on load by the next step, and by
+    get_state)."""
+    from oracle.limiter import positivity_limit
     bcs, st = _dmr_bcs()
     nx, ny = 64, 17
     gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, prec)
@@ -123,12 +125,14 @@ def test_dmr_boundaries_and_limiter(prec, tol):
         u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
     gs.set_state(to_planes(u), 0.0)
     gs.limit(50.0)
-    w = tvb_limit(dg, u, 50.0, 0.0)[0]
+    gs.positivity(1e-10)
+    lim = lambda v, tt: positivity_limit(dg, tvb_limit(dg, v, 50.0, tt)[0], 1e-10)
+    w = lim(u, 0.0)
     t = 0.0
     for _ in range(3):
         dt = gs.cfl_dt(0.16)
         gs.step(dt)
-        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3, limiter=lambda v, tt: tvb_limit(dg, v, 50.0, tt)[0])
+        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3, limiter=lim)
         t += dt
     got = from_planes(gs.get_state())
     assert rel_err(got, w) < tol

@@ -109,3 +109,34 @@ def test_reflective_ghost_negates_normal_momentum():
     a = u[..., 0]
     assert np.allclose(nb["W"][:, 0, 1], -a[:, 0, 1]) and np.allclose(nb["W"][:, 0, 2], a[:, 0, 2])
     assert np.allclose(nb["N"][-1, :, 2], -a[-1, :, 2]) and np.allclose(nb["N"][-1, :, 1], a[-1, :, 1])
+
+
+# -- positivity-preserving scaling (Zhang and Shu 2010; an option outside the paper) --------
+def test_positivity_scaling_closed_form_density():
+    """P^1 density rho = rb + s xi with s > rb: the smallest point value is at
+    the east/west faces, rb - s, so theta_1 = (rb - eps) / s exactly."""
+    from oracle.limiter import positivity_limit
+    dg = DG2D(1, 1, (0, 1, 0, 1), 1, "P", Euler(1.4, 2), PER)
+    rb, s, eps = 1.0, 3.0, 1e-10
+    u = np.zeros((1, 1, 4, 3))
+    u[0, 0, :, 0] = inp.conserved(rb, 0.0, 0.0, 10.0)
+    u[0, 0, 0, 1] = s
+    v = positivity_limit(dg, u, eps)
+    assert v[0, 0, 0, 1] == pytest.approx(s * (rb - eps) / s, rel=1e-14)
+    assert np.array_equal(v[..., 0], u[..., 0])
+
+
+def test_positivity_scaling_invariants():
+    from oracle.limiter import positivity_limit, positivity_points
+    dg = _euler_dg(n=12)
+    u = inp.random_modal_state(12, 12, 2, "P", "euler", seed=31)
+    assert np.array_equal(positivity_limit(dg, u), u)        # physical data untouched
+    bad = u.copy()
+    bad[..., 1:] *= 40.0                                     # large oscillations: negative p, rho
+    P = positivity_points(dg)
+    uq = np.einsum("yxvm,qm->yxqv", bad, P)
+    assert (dg.phys.primitive(uq)[2] < 0).any()
+    v = positivity_limit(dg, bad, 1e-10)
+    assert np.array_equal(v[..., 0], bad[..., 0])
+    rho, _, p = dg.phys.primitive(np.einsum("yxvm,qm->yxqv", v, P))
+    assert rho.min() >= 1e-10 * (1 - 1e-6) and p.min() >= 1e-10 * (1 - 1e-3) - 1e-12
