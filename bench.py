@@ -227,7 +227,7 @@ def run_reference(args):
                              "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB, %d steps, 1 thread (%s)"
                                        % (nx, ny, n, cpu_model())},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps(line, default=float))
     return 0
 
 
@@ -353,7 +353,7 @@ def main():
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
                 "status": {"code": code, "bits": status, "t_sim": t_sim},
                 "cpu_baseline": cpu}
-        print(json.dumps(line))
+        print(json.dumps(line, default=float))
     s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
