@@ -205,6 +205,31 @@ int crkdg_load(crkdg_ctx* ctx, const char* path);
 const char* crkdg_last_error(void);
 const char* crkdg_version(void);
 
+/* No-allocation reduction (no counterpart in the paper; an interface for
+ * callers that cannot allocate device memory: code inside a framework that
+ * owns the device memory pool, or code that must not allocate while a graph
+ * is captured or inside a real-time loop).  Computes, like crkdg_cfl_dt and
+ * crkdg_conservation, the FP64 maximum wave speed over cell averages
+ * (2D: max (|u|+c)/dx + (|v|+c)/dy; 1D: max (|w|+c)/dx; advection: |beta|/dx
+ * terms) and the totals sum_K |K| ubar_K, without allocating:
+ *   u_dev    device state planes [v][m][y][x] of n_modes modes (caller-owned,
+ *            FP32 or FP64 per `precision`), only read;
+ *   out_dev  device array of 1 + nv doubles (caller-owned): out[0] = max wave
+ *            speed, out[1 + v] = total of variable v; written on `stream`;
+ *   beta     host pointer to (beta_x, beta_y) for advection, else may be NULL.
+ * Asynchronous on `stream`.  Scratch: a file-scope device array of about
+ * 64 KiB (1024 per-warp slots) that every GPU loading the library holds until
+ * the process exits; the first call on each device looks up its address with
+ * that device current (so make that first call before any stream capture).
+ * Every call shares the array and clears its counter first, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Meshes above 2^30 cells are rejected with CRKDG_EINVAL; errors are reported
+ * by crkdg_noalloc_last_error().  Calls no cudaMalloc/cudaFree. */
+int crkdg_reduce_state_noalloc(const void* u_dev, int dim, int nx, int ny, int n_modes, int physics, int precision,
+                               double dx, double dy, double gamma, const double* beta, double* out_dev,
+                               void* stream);
+const char* crkdg_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,10 @@ _SIGS = {
     "crkdg_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "crkdg_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "crkdg_reduce_state_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                             C.c_void_p, C.c_void_p]),
+    "crkdg_noalloc_last_error": (C.c_char_p, []),
     "crkdg_last_error": (C.c_char_p, []),
     "crkdg_version": (C.c_char_p, []),
 }
