@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcrkdg.so")
+# CRKDG_LIB may point at another build of the same library (e.g. a variant
+# compiled with different launch bounds)
+LIB_PATH = os.environ.get("CRKDG_LIB", os.path.join(HERE, "libcrkdg.so"))
 MAX_STAGES = 6
 
 OK, EINVAL, ENOMEM, ECUDA, ENONPHYSICAL, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6

@@ -19,7 +19,11 @@ ROOT = os.path.dirname(HERE)
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -prec-div/-prec-sqrt/-ftz change single precision only (FP64 code keeps
+# IEEE division and square root): the FP32 path uses the fast reciprocal and
+# square root and flushes subnormals
 FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
+         "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
          "-I", os.path.join(ROOT, "include")]
 
 
