@@ -76,7 +76,12 @@ enum { CRKDG_FN_CONST = 0, CRKDG_FN_SINE = 1, CRKDG_FN_SINE_PROD = 2, CRKDG_FN_D
 enum { CRKDG_SIDE_W = 0, CRKDG_SIDE_E = 1, CRKDG_SIDE_S = 2, CRKDG_SIDE_N = 3 };
 enum { CRKDG_ADVECTION = 0, CRKDG_EULER = 1 };
 enum { CRKDG_BASIS_P = 0, CRKDG_BASIS_Q = 1 };
-enum { CRKDG_F32 = 0, CRKDG_F64 = 1 };
+/* CRKDG_F32C: compensated FP32 state, 2D Euler without limiters.  The state
+ * is kept as hi + lo FP32 pairs; all stage arithmetic runs in FP32 on hi and
+ * only the final update u^{n+1} = u^n + Delta is accumulated exactly, which
+ * removes the per-step rounding of the state itself (the FP32 error of the
+ * increments is O(eps dt) per step, cf. the perturbed-RK result of Sec. 3.3). */
+enum { CRKDG_F32 = 0, CRKDG_F64 = 1, CRKDG_F32C = 2 };
 enum { CRKDG_FLUX_LLF = 0 };   /* Lax--Friedrichs, alpha per face point and stage */
 
 typedef struct {
@@ -204,6 +209,53 @@ int crkdg_load(crkdg_ctx* ctx, const char* path);
 
 const char* crkdg_last_error(void);
 const char* crkdg_version(void);
+
+/* ------------------------------------------------------------------------
+ * Batched ensembles (no counterpart in the paper: many independent 2D Euler
+ * problems advanced together).  Problems have their own mesh size and domain
+ * and share the scheme (k, basis, tableau, gamma, precision), the boundary
+ * types (periodic / outflow / reflect) and the final-stage limiters.  One
+ * batched step launch covers every problem's tiles; each problem keeps its
+ * own t, dt (from its own FP64 wave-speed reduction, eq. (3.4) style), t_end
+ * and status, and stops costing work once it reaches t_end.
+ * ------------------------------------------------------------------------ */
+typedef struct crkdg_batch crkdg_batch;
+typedef struct {
+    int nx, ny;                 /* cells */
+    double x0, x1, y0, y1;      /* domain */
+} crkdg_batch_problem;
+
+/* bc[4]: W, E, S, N types shared by all problems.  Allocates one state for
+ * all problems (two copies), the problem and task tables, per-problem run
+ * states.  stream must be a non-default stream for crkdg_batch_run. */
+int crkdg_batch_create(const crkdg_batch_problem* probs, int n, const int* bc, int k, int basis,
+                       const crkdg_tableau* tab, double gamma, int precision, void* stream, crkdg_batch** out);
+void crkdg_batch_destroy(crkdg_batch* b);
+/* n_problems, total cells, modes per cell, warp tasks per step */
+int crkdg_batch_sizes(const crkdg_batch* b, int* n_problems, long long* total_cells, int* n_modes, int* n_tasks);
+/* per problem: quadrature points xy[cell][q][2]; projection of point values
+ * values[cell][q][4] (sets t = 0); FP64 host planes [v][m][y][x] in and out
+ * (get_state applies a pending limit to the returned copy) */
+int crkdg_batch_quadrature_points(const crkdg_batch* b, int problem, double* xy);
+int crkdg_batch_project_ic(crkdg_batch* b, int problem, const double* values);
+int crkdg_batch_set_state(crkdg_batch* b, int problem, const double* host_state, double t);
+int crkdg_batch_get_state(crkdg_batch* b, int problem, double* host_state);
+/* final-stage limiters for every problem, as crkdg_limit / crkdg_positivity */
+int crkdg_batch_limit(crkdg_batch* b, double M_tvb);
+int crkdg_batch_positivity(crkdg_batch* b, double eps);
+/* Run every problem to t_end with dt = min(cfl / maxspeed, t_end - t) per
+ * problem: a CUDA graph of steps_per_graph batched steps (captured once per
+ * shape, replayed) is launched until all problems are done or max_graphs
+ * graphs ran; *n_done = problems that reached t_end.  Synchronises once per
+ * graph (reads one counter). */
+int crkdg_batch_run(crkdg_batch* b, double cfl, double t_end, int steps_per_graph, int max_graphs, int* n_done);
+int crkdg_batch_problem_info(crkdg_batch* b, int problem, double* t, unsigned long long* steps, unsigned* status);
+/* launch shape (rows per warp segment, warps per block) and its autotuner,
+ * which times one batched step per candidate on the current states (run
+ * states restored afterwards) */
+int crkdg_batch_set_launch(crkdg_batch* b, int seg_rows, int warps_per_block);
+int crkdg_batch_autotune(crkdg_batch* b, double cfl, double* best_us);
+const char* crkdg_batch_last_error(void);
 
 /* No-allocation reduction (no counterpart in the paper; an interface for
  * callers that cannot allocate device memory: code inside a framework that

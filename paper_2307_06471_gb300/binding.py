@@ -22,7 +22,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_DIRICHLET = 0, 1, 2, 3
 FN_CONST, FN_SINE, FN_SINE_PROD, FN_DMR_BOTTOM, FN_DMR_TOP = 0, 1, 2, 3, 4
 ADVECTION, EULER = 0, 1
 BASIS_P, BASIS_Q = 0, 1
-F32, F64 = 0, 1
+F32, F64, F32C = 0, 1, 2
 FLUX_LLF = 0
 ST_NONPHYSICAL, ST_NAN, ST_TIMEOUT = 1, 2, 4
 
@@ -77,7 +77,29 @@ _SIGS = {
     "crkdg_noalloc_last_error": (C.c_char_p, []),
     "crkdg_last_error": (C.c_char_p, []),
     "crkdg_version": (C.c_char_p, []),
+    "crkdg_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(Tableau),
+                                     C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "crkdg_batch_destroy": (None, [C.c_void_p]),
+    "crkdg_batch_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int)]),
+    "crkdg_batch_quadrature_points": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "crkdg_batch_project_ic": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "crkdg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double]),
+    "crkdg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "crkdg_batch_limit": (C.c_int, [C.c_void_p, C.c_double]),
+    "crkdg_batch_positivity": (C.c_int, [C.c_void_p, C.c_double]),
+    "crkdg_batch_run": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "crkdg_batch_problem_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong),
+                                           C.POINTER(C.c_uint)]),
+    "crkdg_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "crkdg_batch_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "crkdg_batch_last_error": (C.c_char_p, []),
 }
+
+
+class BatchProblem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
+                ("y1", C.c_double)]
 
 
 def lib():
@@ -249,3 +271,89 @@ class Solver:
 
     def load(self, path):
         _check(lib().crkdg_load(self.ctx, path.encode()))
+
+
+def _bcheck(code):
+    if code != OK:
+        raise CrkdgError(code, lib().crkdg_batch_last_error().decode())
+
+
+class Batch:
+    """An ensemble of 2D Euler problems advanced together (crkdg_batch_*).
+    problems: list of (nx, ny, (x0, x1, y0, y1))."""
+
+    def __init__(self, problems, k, basis, tableau, precision, bc=(BC_OUTFLOW,) * 4, gamma=1.4, stream=None):
+        L = lib()
+        arr = (BatchProblem * len(problems))()
+        for i, (nx, ny, box) in enumerate(problems):
+            arr[i] = BatchProblem(nx, ny, box[0], box[1], box[2], box[3])
+        self._bc = (C.c_int * 4)(*bc)
+        tab = make_tableau(*tableau) if not isinstance(tableau, Tableau) else tableau
+        self.ptr = C.c_void_p()
+        _bcheck(L.crkdg_batch_create(C.cast(arr, C.c_void_p), len(problems), self._bc, k, basis, C.byref(tab), gamma,
+                                     precision, C.c_void_p(stream) if stream else None, C.byref(self.ptr)))
+        self.problems = problems
+        self.k = k
+        n, nm, nt = C.c_int(), C.c_int(), C.c_int()
+        cells = C.c_longlong()
+        _bcheck(L.crkdg_batch_sizes(self.ptr, C.byref(n), C.byref(cells), C.byref(nm), C.byref(nt)))
+        self.n, self.total_cells, self.n_modes, self.n_tasks = n.value, cells.value, nm.value, nt.value
+
+    def close(self):
+        if self.ptr:
+            lib().crkdg_batch_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def quadrature_points(self, p):
+        nx, ny, _ = self.problems[p]
+        nq = (self.k + 1) ** 2
+        xy = np.empty(nx * ny * nq * 2)
+        _bcheck(lib().crkdg_batch_quadrature_points(self.ptr, p, _dptr(xy)))
+        return xy.reshape(nx * ny, nq, 2)
+
+    def project_function(self, p, fn):
+        xy = self.quadrature_points(p)
+        vals = np.ascontiguousarray(fn(xy[..., 0], xy[..., 1]), dtype=np.float64)
+        _bcheck(lib().crkdg_batch_project_ic(self.ptr, p, _dptr(vals)))
+
+    def set_state(self, p, u, t=0.0):
+        a = np.ascontiguousarray(u, dtype=np.float64)
+        _bcheck(lib().crkdg_batch_set_state(self.ptr, p, _dptr(a), float(t)))
+
+    def get_state(self, p):
+        nx, ny, _ = self.problems[p]
+        a = np.empty((4, self.n_modes, ny, nx))
+        _bcheck(lib().crkdg_batch_get_state(self.ptr, p, _dptr(a)))
+        return a
+
+    def limit(self, M):
+        _bcheck(lib().crkdg_batch_limit(self.ptr, float(M)))
+
+    def positivity(self, eps):
+        _bcheck(lib().crkdg_batch_positivity(self.ptr, float(eps)))
+
+    def run(self, cfl, t_end, steps_per_graph=8, max_graphs=1):
+        d = C.c_int()
+        _bcheck(lib().crkdg_batch_run(self.ptr, float(cfl), float(t_end), int(steps_per_graph), int(max_graphs),
+                                      C.byref(d)))
+        return d.value
+
+    def info(self, p):
+        t, st = C.c_double(), C.c_uint()
+        n = C.c_ulonglong()
+        _bcheck(lib().crkdg_batch_problem_info(self.ptr, p, C.byref(t), C.byref(n), C.byref(st)))
+        return t.value, n.value, st.value
+
+    def set_launch(self, seg_rows=0, warps_per_block=0):
+        _bcheck(lib().crkdg_batch_set_launch(self.ptr, int(seg_rows), int(warps_per_block)))
+
+    def autotune(self, cfl):
+        us = C.c_double()
+        _bcheck(lib().crkdg_batch_autotune(self.ptr, float(cfl), C.byref(us)))
+        return us.value

@@ -50,6 +50,7 @@ struct crkdg_ctx {
     int nv, nm, nqv;
     size_t ncell, elems;
     size_t esize;
+    int planes;
     void* u[2];
     int cur;
     double* d_tab;
@@ -219,7 +220,10 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
     if (basis != CRKDG_BASIS_P && basis != CRKDG_BASIS_Q) return fail(CRKDG_EINVAL, "basis must be P or Q");
     if (flux != CRKDG_FLUX_LLF) return fail(CRKDG_EINVAL, "flux must be CRKDG_FLUX_LLF");
     if (physics != CRKDG_ADVECTION && physics != CRKDG_EULER) return fail(CRKDG_EINVAL, "unknown physics");
-    if (precision != CRKDG_F32 && precision != CRKDG_F64) return fail(CRKDG_EINVAL, "unknown precision");
+    if (precision != CRKDG_F32 && precision != CRKDG_F64 && precision != CRKDG_F32C)
+        return fail(CRKDG_EINVAL, "unknown precision");
+    if (precision == CRKDG_F32C && (physics != CRKDG_EULER || mesh->dim != 2))
+        return fail(CRKDG_EUNSUPPORTED, "the compensated FP32 state is built for 2D Euler");
     if (tab->s < 1 || tab->s > CRKDG_MAX_STAGES) return fail(CRKDG_EINVAL, "tableau stages must be 1..6");
     for (int i = 0; i < tab->s; ++i)
         for (int j = i; j < CRKDG_MAX_STAGES; ++j)
@@ -263,7 +267,8 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
     c->nqv = mesh->dim == 1 ? k + 1 : (k + 1) * (k + 1);
     c->ncell = (size_t)c->mesh.nx * c->mesh.ny;
     c->elems = c->ncell * c->nv * c->nm;
-    c->esize = precision == CRKDG_F32 ? 4 : 8;
+    c->esize = precision == CRKDG_F64 ? 8 : 4;
+    c->planes = precision == CRKDG_F32C ? 2 : 1;   // compensated: hi planes then lo planes
     c->kphys = physics == CRKDG_ADVECTION ? crk::PHYS_ADV : (mesh->dim == 1 ? crk::PHYS_EULER1D : crk::PHYS_EULER);
     c->stream = static_cast<cudaStream_t>(stream);
     c->t = 0.0;
@@ -276,9 +281,9 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
         return code;
     };
     for (int b = 0; b < 2; ++b) {
-        if (cudaMalloc(&c->u[b], c->elems * c->esize) != cudaSuccess)
+        if (cudaMalloc(&c->u[b], c->elems * c->esize * c->planes) != cudaSuccess)
             return bail(fail(CRKDG_ENOMEM, "cudaMalloc of the state failed"));
-        cudaMemsetAsync(c->u[b], 0, c->elems * c->esize, c->stream);
+        cudaMemsetAsync(c->u[b], 0, c->elems * c->esize * c->planes, c->stream);
     }
     double htab[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
     for (int i = 0; i < crk::MAXS * crk::MAXS; ++i) htab[i] = tab->a[i];
@@ -374,9 +379,12 @@ int crkdg_set_state(crkdg_ctx* c, const double* h, double t) {
     if (c->precision == CRKDG_F64) {
         CK(cudaMemcpyAsync(c->u[c->cur], h, c->elems * 8, cudaMemcpyHostToDevice, c->stream));
     } else {
-        std::vector<float> f(c->elems);
-        for (size_t i = 0; i < c->elems; ++i) f[i] = (float)h[i];
-        CK(cudaMemcpyAsync(c->u[c->cur], f.data(), c->elems * 4, cudaMemcpyHostToDevice, c->stream));
+        std::vector<float> f(c->elems * c->planes);
+        for (size_t i = 0; i < c->elems; ++i) {
+            f[i] = (float)h[i];
+            if (c->planes == 2) f[c->elems + i] = (float)(h[i] - (double)f[i]);
+        }
+        CK(cudaMemcpyAsync(c->u[c->cur], f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     c->t = t;
@@ -403,10 +411,10 @@ int crkdg_get_state(crkdg_ctx* c, double* h) {
         CK(cudaMemcpyAsync(h, c->u[c->cur], c->elems * 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {
-        std::vector<float> f(c->elems);
-        CK(cudaMemcpyAsync(f.data(), c->u[c->cur], c->elems * 4, cudaMemcpyDeviceToHost, c->stream));
+        std::vector<float> f(c->elems * c->planes);
+        CK(cudaMemcpyAsync(f.data(), c->u[c->cur], f.size() * 4, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < c->elems; ++i) h[i] = f[i];
+        for (size_t i = 0; i < c->elems; ++i) h[i] = c->planes == 2 ? (double)f[i] + (double)f[c->elems + i] : f[i];
     }
     return CRKDG_OK;
 }
@@ -549,6 +557,8 @@ int crkdg_run_fixed(crkdg_ctx* c, int n_steps, double dt) {
 int crkdg_limit(crkdg_ctx* c, double M) {
     if (check_ctx(c)) return CRKDG_EINVAL;
     if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "the TVB limiter is built for 2D meshes");
+    if (c->precision == CRKDG_F32C && M >= 0.0)
+        return fail(CRKDG_EUNSUPPORTED, "limiters are not built for the compensated FP32 state");
     if (M >= 0.0) {
         c->limiter_on = true;
         c->M = M;
@@ -566,6 +576,8 @@ int crkdg_positivity(crkdg_ctx* c, double eps) {
     if (check_ctx(c)) return CRKDG_EINVAL;
     if (c->dim != 2 || c->physics != CRKDG_EULER)
         return fail(CRKDG_EUNSUPPORTED, "positivity scaling is built for 2D Euler");
+    if (c->precision == CRKDG_F32C && eps > 0.0)
+        return fail(CRKDG_EUNSUPPORTED, "limiters are not built for the compensated FP32 state");
     if (eps > 0.0) {
         c->pp_eps = eps;
         if (!c->pending) {

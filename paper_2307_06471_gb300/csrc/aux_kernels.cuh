@@ -10,7 +10,7 @@ namespace crk {
 // max_K wave speed (2D: s_x/dx + s_y/dy; 1D: |f'|/dx) and sum_K |K| ubar_K,
 // from the mode-0 planes.  Per-warp slots, then the last warp reduces them in
 // a fixed order (deterministic) and writes DevState.
-template <class T, int PHYS, int NV>
+template <class T, int PHYS, int NV, bool COMP = false>
 __global__ void reduce_state_kernel(const T* __restrict__ u, int nx, int ny, int nm, double dx, double dy,
                                     double gamma, double bx, double by, DevState* ds, double* partials,
                                     int set_dt) {
@@ -27,6 +27,7 @@ __global__ void reduce_state_kernel(const T* __restrict__ u, int nx, int ny, int
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             av[v] = double(u[(size_t)(v * nm) * plane + c]);
+            if (COMP) av[v] += double(u[(size_t)(NV * nm) * plane + (size_t)(v * nm) * plane + c]);
             sm[v] += av[v];
         }
         double sp;
@@ -98,7 +99,8 @@ __global__ void reduce_state_kernel(const T* __restrict__ u, int nx, int ny, int
 }
 
 // u_m = sum_q pw[q][m] g(x_q) per cell, values[cell][q][v] (FP64, device).
-template <class T, int K, int B, int NV>
+// COMP: store hi = T(u_m) and lo = T(u_m - hi) in the planes after the hi planes.
+template <class T, int K, int B, int NV, bool COMP = false>
 __global__ void project2d_kernel(const double* __restrict__ vals, T* __restrict__ u, int ncell) {
     constexpr Tab2D<K, B> tb = make_tab2d<K, B>();
     constexpr int NQV = Tab2D<K, B>::NQV, NM = Tab2D<K, B>::NM;
@@ -112,7 +114,9 @@ __global__ void project2d_kernel(const double* __restrict__ vals, T* __restrict_
             double s = 0.0;
 #pragma unroll
             for (int q = 0; q < NQV; ++q) s += tb.pw[q][m] * vals[((size_t)c * NQV + q) * NV + v];
-            u[(size_t)(v * NM + m) * plane + c] = T(s);
+            const T hi = T(s);
+            u[(size_t)(v * NM + m) * plane + c] = hi;
+            if (COMP) u[(size_t)(NV * NM) * plane + (size_t)(v * NM + m) * plane + c] = T(s - double(hi));
         }
 }
 

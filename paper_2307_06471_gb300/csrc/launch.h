@@ -38,6 +38,23 @@ cudaError_t launch_reduce(int dim, int phys, int prec, const void* u, int nx, in
     cudaError_t limit2d_##NAME(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,  \
                                cudaStream_t st);                                                         \
     cudaError_t project2d_##NAME(int k, int basis, const double* vals, void* u, int ncell, cudaStream_t st);
+// compensated FP32 state (hi + lo planes), 2D Euler only
+cudaError_t step2d_euler_f32c(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t info2d_euler_f32c(int k, int basis, int s, KernelInfo* info);
+cudaError_t project2d_euler_f32c(int k, int basis, const double* vals, void* u, int ncell, cudaStream_t st);
+cudaError_t reduce_euler_f32c(const void* u, int nx, int ny, int nm, double dx, double dy, double gamma, DevState* ds,
+                              double* partials, int blocks, int set_dt, cudaStream_t st);
+
+struct BatchProblem;
+#define CRK_DECL_B(NAME)                                                                                     \
+    cudaError_t batch2d_##NAME(int k, int basis, const StepArgs& a, const BatchProblem* probs, const int2* tasks, \
+                               int n_tasks, DevState* states, int* curs, unsigned* done, const void* bufA,    \
+                               void* bufB, int wpb, cudaStream_t st);                                         \
+    cudaError_t binfo2d_##NAME(int k, int basis, int s, KernelInfo* info);
+CRK_DECL_B(euler_f32)
+CRK_DECL_B(euler_f64)
+#undef CRK_DECL_B
+
 CRK_DECL_2D(euler_f32)
 CRK_DECL_2D(euler_f64)
 CRK_DECL_2D(adv_f32)

@@ -42,8 +42,30 @@ struct Step2D {
     }
 };
 
-template <class T, int K, int B, int PHYS>
-__global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
+// Per-problem view of one step: the single-problem kernel builds it from
+// its launch arguments, the batched kernel from the problem table.
+template <class T>
+struct ProbView {
+    const T* uin;
+    T* uout;
+    int nx, ny;
+    double x0, y0, dx, dy;
+    double t, dt;
+    int n_strips, n_segs, seg_len, total_warps;
+    double* partials;     // this problem's per-warp reduction slots
+    DevState* ds;         // this problem's run state
+    int* cur;             // batched runs: this problem's buffer index (flipped by its last warp)
+    unsigned* done;       // batched runs: count of problems that reached t_end
+    int copy_if_idle;     // single-problem runs copy u^n when dt <= 0
+};
+
+// COMP = true: compensated FP32 state.  The buffers hold hi planes followed
+// by lo planes (u = hi + lo); every stage computes in T from hi, and only the
+// final update u^{n+1} = u^n + Delta is accumulated exactly (TwoSum of hi and
+// Delta + lo), so the state does not collect one rounding of its own size
+// per step.  Used without limiters.
+template <class T, int K, int B, int PHYS, bool COMP = false>
+__device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>& pv, const int gw) {
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
     constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
@@ -59,20 +81,18 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
     auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
 
     const int lane = tid & 31;
-    const int gw = blockIdx.x * (nthr >> 5) + (tid >> 5);
-    const int total_warps = a.n_strips * a.n_segs;
-    if (gw >= total_warps) return;   // whole warp leaves; no block barriers below
+    const int total_warps = pv.total_warps;
 
-    const int nx = a.nx, ny = a.ny;
+    const int nx = pv.nx, ny = pv.ny;
     const size_t plane = (size_t)nx * ny;
-    const T* __restrict__ uin = static_cast<const T*>(a.uin);
-    T* __restrict__ uout = static_cast<T*>(a.uout);
+    const T* __restrict__ uin = pv.uin;
+    T* __restrict__ uout = pv.uout;
 
-    const double dt = a.dt_from_dev ? a.ds->dt : a.dt;
-    const double t0 = a.dt_from_dev ? a.ds->t : a.t;
+    const double dt = pv.dt;
+    const double t0 = pv.t;
 
-    const int strip = gw % a.n_strips;
-    const int seg = gw / a.n_strips;
+    const int strip = gw % pv.n_strips;
+    const int seg = gw / pv.n_strips;
     const int xs = strip * 30;
     const int col = xs - 1 + lane;
     const bool perx = a.bc[0].type == BC_PERIODIC;
@@ -83,16 +103,17 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
     const bool has_bcW = !perx && xs == 0;
     const bool has_bcE = !perx && xs + 30 >= nx;
 
-    const int r0 = seg * a.seg_len;
-    const int r1 = min(r0 + a.seg_len, ny);
+    const int r0 = seg * pv.seg_len;
+    const int r1 = min(r0 + pv.seg_len, ny);
     const int rstart = (r0 > 0 || pery) ? r0 - 1 : r0;
     const int rend = (r1 < ny || pery) ? r1 : r1 - 1;
 
     // a non-positive dt leaves the state unchanged (runs past t_end)
     if (!(dt > 0.0)) {
-        if (outlane)
+        if (pv.copy_if_idle && outlane)
             for (int r = r0; r < r1; ++r)
-                for (int d = 0; d < C::NDOF; ++d) uout[d * plane + (size_t)r * nx + col] = uin[d * plane + (size_t)r * nx + col];
+                for (int d = 0; d < (COMP ? 2 : 1) * C::NDOF; ++d)
+                    uout[d * plane + (size_t)r * nx + col] = uin[d * plane + (size_t)r * nx + col];
         return;
     }
 
@@ -104,9 +125,9 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
         ph.bx = T(a.beta[0]);
         ph.by = T(a.beta[1]);
     }
-    const T rx = T(1.0 / a.dx), ry = T(1.0 / a.dy);
+    const T rx = T(1.0 / pv.dx), ry = T(1.0 / pv.dy);
     const T tdt = T(dt);
-    const T Mdx2 = T(a.M * a.dx * a.dx), Mdy2 = T(a.M * a.dy * a.dy);
+    const T Mdx2 = T(a.M * pv.dx * pv.dx), Mdy2 = T(a.M * pv.dy * pv.dy);
     const T gam = T(a.gamma);
 
     // reduction accumulators (FP64)
@@ -134,8 +155,8 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = r < 0 ? 2 : 3;
-            const double xc = a.x0 + (col + 0.5) * a.dx;
-            const double yc = r < 0 ? a.y0 - 0.5 * a.dy : a.y0 + (ny + 0.5) * a.dy;
+            const double xc = pv.x0 + (col + 0.5) * pv.dx;
+            const double yc = r < 0 ? pv.y0 - 0.5 * pv.dy : pv.y0 + (ny + 0.5) * pv.dy;
             bc_exterior<T, NV>(a.bc[side], 1, own, xc, yc, t0, out);
         }
     };
@@ -150,8 +171,8 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = c < 0 ? 0 : 1;
-            const double xc = c < 0 ? a.x0 - 0.5 * a.dx : a.x0 + (nx + 0.5) * a.dx;
-            const double yc = a.y0 + (r + 0.5) * a.dy;
+            const double xc = c < 0 ? pv.x0 - 0.5 * pv.dx : pv.x0 + (nx + 0.5) * pv.dx;
+            const double yc = pv.y0 + (r + 0.5) * pv.dy;
             bc_exterior<T, NV>(a.bc[side], 0, own, xc, yc, t0, out);
         }
     };
@@ -163,7 +184,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
         const bool south_bc = (r == 0) && !pery;
         const bool do_south = (r > rstart) || south_bc;   // flux through this row's south face
         const bool keep_north = r < rend || (r == ny - 1 && !pery && out_row);
-        const double yc = a.y0 + (ry_ + 0.5) * a.dy;
+        const double yc = pv.y0 + (ry_ + 0.5) * pv.dy;
 
         // ---- load u^n (and limit on load) -------------------------------------
         T un[NV][NM];
@@ -319,12 +340,12 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
                 if (has_bcW && lane == 0) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], a.x0, yc + 0.5 * a.dy * tb.xq[p], ti, tE[p]);
+                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0, yc + 0.5 * pv.dy * tb.xq[p], ti, tE[p]);
                 }
                 if (has_bcE && col == nx - 1) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], a.x0 + nx * a.dx, yc + 0.5 * a.dy * tb.xq[p], ti,
+                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0 + nx * pv.dx, yc + 0.5 * pv.dy * tb.xq[p], ti,
                                            tWn[p]);
                 }
 #pragma unroll
@@ -341,8 +362,8 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
                 for (int p = 0; p < NQ; ++p) {
                     T lo[NV];
                     if (south_bc) {
-                        const double xp = a.x0 + (col + 0.5) * a.dx + 0.5 * a.dx * tb.xq[p];
-                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, a.y0, ti, lo);
+                        const double xp = pv.x0 + (col + 0.5) * pv.dx + 0.5 * pv.dx * tb.xq[p];
+                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0, ti, lo);
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
@@ -366,27 +387,45 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
             // write u^{n+1} of row rw and accumulate the FP64 reductions
             if (!outlane) return;
             const size_t o = (size_t)rw * nx + col;
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
             double av[NV];
+            if constexpr (COMP) {
+                // P holds Delta: u^{n+1} = (hi + lo) + Delta, hi' + lo' by TwoSum
+                const size_t lo_off = (size_t)C::NDOF * plane;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                av[v] = double(P[v][0]);
-                red_sum[v] += av[v];
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        const size_t ix = (size_t)(v * NM + m) * plane + o;
+                        const T hi = uin[ix], lo = uin[lo_off + ix];
+                        const T d = P[v][m] + lo;
+                        const T sum = hi + d;
+                        const T bv = sum - hi;
+                        const T err = (hi - (sum - bv)) + (d - bv);
+                        uout[ix] = sum;
+                        uout[lo_off + ix] = err;
+                        if (m == 0) av[v] = double(sum) + double(err);
+                    }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) av[v] = double(P[v][0]);
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) red_sum[v] += av[v];
             double sp;
             if constexpr (PHYS == PHYS_EULER) {
                 const double ir = 1.0 / av[0];
                 const double w = av[1] * ir, vv = av[2] * ir;
                 const double p = (a.gamma - 1.0) * (av[3] - 0.5 * (av[1] * w + av[2] * vv));
                 const double c = sqrt(fmax(a.gamma * p * ir, 0.0));
-                sp = (fabs(w) + c) / a.dx + (fabs(vv) + c) / a.dy;
+                sp = (fabs(w) + c) / pv.dx + (fabs(vv) + c) / pv.dy;
                 if (!(av[0] > 0.0) || !(p > 0.0)) status |= ST_NONPHYSICAL;
                 if (!(sp == sp)) status |= ST_NAN;
             } else {
-                sp = fabs(a.beta[0]) / a.dx + fabs(a.beta[1]) / a.dy;
+                sp = fabs(a.beta[0]) / pv.dx + fabs(a.beta[1]) / pv.dy;
                 if (!(av[0] == av[0])) status |= ST_NAN;
             }
             red_max = fmax(red_max, sp);
@@ -423,7 +462,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
                     sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
                     sy -= FS[p][v] * T(tb.pS[p][m]);
                 }
-                P[v][m] = un[v][m] - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V[v][m]);
+                P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V[v][m]);
             }
         if (r == ny - 1 && !pery) {
             // top boundary: north face flux from the stored north traces
@@ -442,8 +481,8 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
                     T lo[NV], hi[NV], F[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
-                    const double xp = a.x0 + (col + 0.5) * a.dx + 0.5 * a.dx * tb.xq[p];
-                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, a.y0 + ny * a.dy, ti, hi);
+                    const double xp = pv.x0 + (col + 0.5) * pv.dx + 0.5 * pv.dx * tb.xq[p];
+                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, pv.y0 + ny * pv.dy, ti, hi);
                     llf<T, PHYS, 1>(ph, lo, hi, F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FN[p][v] += bi * F[v];
@@ -468,7 +507,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
     }
 
     // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
-    const double cell = a.dx * a.dy;
+    const double cell = pv.dx * pv.dy;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
@@ -477,16 +516,16 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
         red_trouble += __shfl_xor_sync(0xffffffffu, red_trouble, off);
         status |= __shfl_xor_sync(0xffffffffu, status, off);
     }
-    double* slotp = a.partials + (size_t)gw * C::NRED;
+    double* slotp = pv.partials + (size_t)gw * C::NRED;
     unsigned prev = 0;
     if (lane == 0) {
         slotp[0] = red_max;
 #pragma unroll
         for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
         slotp[1 + NV] = double(red_trouble);
-        if (status) atomicOr(&a.ds->status, status);
+        if (status) atomicOr(&pv.ds->status, status);
         __threadfence();
-        prev = atomicAdd(&a.ds->counter, 1u);
+        prev = atomicAdd(&pv.ds->counter, 1u);
     }
     prev = __shfl_sync(0xffffffffu, prev, 0);
     if (prev != (unsigned)total_warps - 1) return;
@@ -496,7 +535,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
     for (int wi = lane; wi < total_warps; wi += 32) {
-        const double* q = a.partials + (size_t)wi * C::NRED;
+        const double* q = pv.partials + (size_t)wi * C::NRED;
         mx = fmax(mx, __ldcg(q));
 #pragma unroll
         for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
@@ -510,7 +549,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
         tr += __shfl_xor_sync(0xffffffffu, tr, off);
     }
     if (lane == 0) {
-        DevState* ds = a.ds;
+        DevState* ds = pv.ds;
         ds->maxspeed = mx;
 #pragma unroll
         for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
@@ -519,11 +558,93 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
         ds->t = tn;
         double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
         const double rem = ds->t_end - tn;
+        const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
         if (dn > rem) dn = rem;
+        if (reached) dn = 0.0;
         ds->dt = dn;
         ds->steps += 1;
         ds->counter = 0;
+        if (pv.cur) *pv.cur ^= 1;
+        if (pv.done && reached) atomicAdd(pv.done, 1u);
     }
+}
+
+// One problem: the launch arguments describe the mesh; dt and t come from
+// the arguments or from the device run state (device-driven runs).
+template <class T, int K, int B, int PHYS, bool COMP = false>
+__global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
+    ProbView<T> pv;
+    pv.uin = static_cast<const T*>(a.uin);
+    pv.uout = static_cast<T*>(a.uout);
+    pv.nx = a.nx;
+    pv.ny = a.ny;
+    pv.x0 = a.x0;
+    pv.y0 = a.y0;
+    pv.dx = a.dx;
+    pv.dy = a.dy;
+    pv.t = a.dt_from_dev ? a.ds->t : a.t;
+    pv.dt = a.dt_from_dev ? a.ds->dt : a.dt;
+    pv.n_strips = a.n_strips;
+    pv.n_segs = a.n_segs;
+    pv.seg_len = a.seg_len;
+    pv.total_warps = a.n_strips * a.n_segs;
+    pv.partials = a.partials;
+    pv.ds = a.ds;
+    pv.cur = nullptr;
+    pv.done = nullptr;
+    pv.copy_if_idle = 1;
+    step2d_body<T, K, B, PHYS, COMP>(a, pv, gw);
+}
+
+// Batched ensemble: problems of different sizes and domains share the
+// scheme, tableau and boundary types; each has its own state slice, run state
+// (t, dt from its own FP64 wave-speed reduction, t_end, status) and buffer
+// index.  Warps take (problem, warp) tasks from a flattened table.  A problem
+// whose dt is 0 (it reached t_end) costs nothing: its warps return at once.
+struct BatchProblem {
+    long long offset;      // element offset of the problem's planes in each buffer
+    int nx, ny;
+    double x0, y0, dx, dy;
+    int n_strips, n_segs;
+    int warp0;             // first task / reduction slot of the problem
+};
+
+template <class T, int K, int B, int PHYS>
+__global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, const BatchProblem* __restrict__ probs,
+                                                           const int2* __restrict__ tasks, int n_tasks,
+                                                           DevState* states, int* curs, unsigned* done,
+                                                           const T* bufA, T* bufB) {
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= n_tasks) return;
+    const int2 tk = tasks[gw];
+    const BatchProblem pb = probs[tk.x];
+    DevState* ds = states + tk.x;
+    const int cur = curs[tk.x];
+    ProbView<T> pv;
+    T* A = const_cast<T*>(bufA) + pb.offset;
+    T* Bb = bufB + pb.offset;
+    pv.uin = cur ? Bb : A;
+    pv.uout = cur ? A : Bb;
+    pv.nx = pb.nx;
+    pv.ny = pb.ny;
+    pv.x0 = pb.x0;
+    pv.y0 = pb.y0;
+    pv.dx = pb.dx;
+    pv.dy = pb.dy;
+    pv.t = ds->t;
+    pv.dt = ds->dt;
+    pv.n_strips = pb.n_strips;
+    pv.n_segs = pb.n_segs;
+    pv.seg_len = a.seg_len;
+    pv.total_warps = pb.n_strips * pb.n_segs;
+    pv.partials = a.partials + (size_t)pb.warp0 * Step2D<T, K, B, PHYS>::NRED;
+    pv.ds = ds;
+    pv.cur = curs + tk.x;
+    pv.done = done;
+    pv.copy_if_idle = 0;
+    step2d_body<T, K, B, PHYS>(a, pv, tk.y);
 }
 
 }  // namespace crk
