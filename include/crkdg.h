@@ -256,6 +256,45 @@ int crkdg_batch_problem_info(crkdg_batch* b, int problem, double* t, unsigned lo
 int crkdg_batch_set_launch(crkdg_batch* b, int seg_rows, int warps_per_block);
 int crkdg_batch_autotune(crkdg_batch* b, double cfl, double* best_us);
 const char* crkdg_batch_last_error(void);
+/* features and TVB labels of one problem's stored state (see crkdg_features) */
+int crkdg_batch_features(crkdg_batch* b, int problem, float* X_dev, float* y_dev, double M_tvb);
+
+/* ------------------------------------------------------------------------
+ * Learned troubled-cell indicator (no counterpart in the paper).  A network
+ * 40 -> 64 -> 64 -> 64 -> 1 (ReLU) gives a logit per cell from 40 features
+ * of the cell: per conserved variable q, the four neighbour-average
+ * differences (E, W, N, S) and the five non-constant P^2 modes divided by
+ * their largest magnitude s_q, then log10(s_q / (M h^2)) clipped to [-8, 8]
+ * (h = max(dx, dy)).  Parameters: FP32 vector of crkdg_mlp_n_params() values,
+ * order W1 b1 W2 b2 W3 b3 W4 b4, W row-major (out x in).  Training runs FP32
+ * kernels (class-weighted BCE, Adam); inference runs BF16 weights and
+ * activations with FP32 accumulation on the tensor cores.
+ * ------------------------------------------------------------------------ */
+typedef struct crkdg_mlp crkdg_mlp;
+int crkdg_mlp_create(unsigned long long seed, void* stream, crkdg_mlp** out);   /* He-normal init */
+void crkdg_mlp_destroy(crkdg_mlp* m);
+int crkdg_mlp_n_params(void);
+int crkdg_mlp_set_params(crkdg_mlp* m, const float* host_params);   /* also resets Adam state */
+int crkdg_mlp_get_params(const crkdg_mlp* m, float* host_params);
+/* mean loss -[pw y log s(z) + (1-y) log(1-s(z))] over n samples (X_dev
+ * [n][40], y_dev [n] in {0,1}, device FP32) and its gradient (host, may be NULL) */
+int crkdg_mlp_loss_grad(crkdg_mlp* m, const float* X_dev, const float* y_dev, int n, double pos_weight,
+                        double* loss, float* grad_host);
+/* epochs of minibatch Adam (lr, beta = 0.9/0.999, eps = 1e-8) over a seeded
+ * shuffle; *last_epoch_loss = mean minibatch loss of the last epoch */
+int crkdg_mlp_train(crkdg_mlp* m, const float* X_dev, const float* y_dev, int n, int epochs, int batch, double lr,
+                    double pos_weight, unsigned long long seed, double* last_epoch_loss);
+/* logits_dev[n] from X_dev[n][40] (tensor-core inference) */
+int crkdg_mlp_predict(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev);
+const char* crkdg_mlp_last_error(void);
+/* features X_dev[cell][40] and TVB labels y_dev[cell] (1 = the TVB-minmod
+ * test with parameter M flags the cell) of the context's stored state */
+int crkdg_features(crkdg_ctx* ctx, float* X_dev, float* y_dev, double M_tvb);
+/* Use the network as the troubled-cell test of the final-stage limiter:
+ * limit when the logit > z_hi, keep when < z_lo, TVB test in between (the
+ * reconstruction is always the TVB-minmod one).  net = NULL: TVB test only.
+ * 2D Euler, k = 2, FP32; net must outlive its use. */
+int crkdg_set_indicator(crkdg_ctx* ctx, const crkdg_mlp* net, double z_lo, double z_hi);
 
 /* No-allocation reduction (no counterpart in the paper; an interface for
  * callers that cannot allocate device memory: code inside a framework that

@@ -76,8 +76,11 @@ def neighbour_averages(dg, avg, t):
     return nb
 
 
-def tvb_limit(dg, u, M, t):
-    """Return (limited copy of u, boolean troubled-cell map)."""
+def tvb_limit(dg, u, M, t, force=None):
+    """Return (limited copy of u, boolean troubled-cell map).  ``force``
+    (optional boolean map) replaces the TVB troubled-cell test: the cells it
+    marks get the TVB-minmod reconstruction, the others are kept (the way a
+    learned indicator's decisions are applied)."""
     u = np.array(u, dtype=np.float64, copy=True)
     if dg.B.nm < 3:
         return u, np.zeros((dg.ny, dg.nx), dtype=bool)
@@ -102,7 +105,7 @@ def tvb_limit(dg, u, M, t):
                 cx, cy = list(ax), list(ay)
             mx = tvb_minmod(cx[0], cx[1], cx[2], M * dg.dx * dg.dx)
             my = tvb_minmod(cy[0], cy[1], cy[2], M * dg.dy * dg.dy)
-            flags[y, x] = bool(np.any(mx != cx[0]) or np.any(my != cy[0]))
+            flags[y, x] = bool(np.any(mx != cx[0]) or np.any(my != cy[0])) if force is None else bool(force[y, x])
             newx[y, x] = Rx @ mx if systems else mx
             newy[y, x] = Ry @ my if systems else my
     out = u.copy()

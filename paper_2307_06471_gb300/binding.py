@@ -94,6 +94,20 @@ _SIGS = {
     "crkdg_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "crkdg_batch_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "crkdg_batch_last_error": (C.c_char_p, []),
+    "crkdg_batch_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double]),
+    "crkdg_mlp_create": (C.c_int, [C.c_ulonglong, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "crkdg_mlp_destroy": (None, [C.c_void_p]),
+    "crkdg_mlp_n_params": (C.c_int, []),
+    "crkdg_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "crkdg_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "crkdg_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_float)]),
+    "crkdg_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                  C.c_double, C.c_ulonglong, C.POINTER(C.c_double)]),
+    "crkdg_mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "crkdg_mlp_last_error": (C.c_char_p, []),
+    "crkdg_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
+    "crkdg_set_indicator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
 }
 
 
@@ -266,6 +280,14 @@ class Solver:
         _check(lib().crkdg_autotune(self.ctx, C.byref(us)))
         return us.value
 
+    def features(self, X_ptr, y_ptr, M):
+        """Features [cells, 40] and TVB labels [cells] into device buffers
+        (raw pointers, e.g. torch data_ptr())."""
+        _check(lib().crkdg_features(self.ctx, C.c_void_p(X_ptr), C.c_void_p(y_ptr), float(M)))
+
+    def set_indicator(self, net, z_lo=-1.3862943611198906, z_hi=1.3862943611198906):
+        _check(lib().crkdg_set_indicator(self.ctx, net.ptr if net is not None else None, float(z_lo), float(z_hi)))
+
     def save(self, path):
         _check(lib().crkdg_save(self.ctx, path.encode()))
 
@@ -357,3 +379,58 @@ class Batch:
         us = C.c_double()
         _bcheck(lib().crkdg_batch_autotune(self.ptr, float(cfl), C.byref(us)))
         return us.value
+
+    def features(self, p, X_ptr, y_ptr, M):
+        _bcheck(lib().crkdg_batch_features(self.ptr, p, C.c_void_p(X_ptr), C.c_void_p(y_ptr), float(M)))
+
+
+def _mcheck(code):
+    if code != OK:
+        raise CrkdgError(code, lib().crkdg_mlp_last_error().decode())
+
+
+class MLP:
+    """The learned troubled-cell indicator network (crkdg_mlp_*).  X/y/logit
+    arguments are device pointers (e.g. torch tensors' data_ptr())."""
+
+    def __init__(self, seed=0, stream=None):
+        self.ptr = C.c_void_p()
+        _mcheck(lib().crkdg_mlp_create(seed, C.c_void_p(stream) if stream else None, C.byref(self.ptr)))
+        self.n_params = lib().crkdg_mlp_n_params()
+
+    def close(self):
+        if self.ptr:
+            lib().crkdg_mlp_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        a = np.empty(self.n_params, dtype=np.float32)
+        _mcheck(lib().crkdg_mlp_get_params(self.ptr, a.ctypes.data_as(C.POINTER(C.c_float))))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.n_params
+        _mcheck(lib().crkdg_mlp_set_params(self.ptr, a.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def loss_grad(self, X_ptr, y_ptr, n, pos_weight=1.0):
+        loss = C.c_double()
+        g = np.empty(self.n_params, dtype=np.float32)
+        _mcheck(lib().crkdg_mlp_loss_grad(self.ptr, C.c_void_p(X_ptr), C.c_void_p(y_ptr), int(n), float(pos_weight),
+                                          C.byref(loss), g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def train(self, X_ptr, y_ptr, n, epochs, batch, lr, pos_weight=1.0, seed=0):
+        loss = C.c_double()
+        _mcheck(lib().crkdg_mlp_train(self.ptr, C.c_void_p(X_ptr), C.c_void_p(y_ptr), int(n), int(epochs), int(batch),
+                                      float(lr), float(pos_weight), seed, C.byref(loss)))
+        return loss.value
+
+    def predict(self, X_ptr, n, out_ptr):
+        _mcheck(lib().crkdg_mlp_predict(self.ptr, C.c_void_p(X_ptr), int(n), C.c_void_p(out_ptr)))

@@ -18,6 +18,10 @@
 using crk::DevState;
 using crk::StepArgs;
 
+const float* crkdg_mlp_device_params(const crkdg_mlp* m);
+int crkdg_features_impl(const StepArgs& a, int precision, int k, int basis, const void* u, float* X, float* y,
+                        double Mh2, cudaStream_t st);
+
 namespace {
 
 thread_local std::string g_err;
@@ -69,6 +73,8 @@ struct crkdg_ctx {
     double pp_pending;    // positivity floor of the pending limit
     int seg_rows, wpb;
     int kphys;   // kernel physics id
+    const float* mlp = nullptr;   // learned indicator parameters (device), owned by a crkdg_mlp
+    float mlp_zlo = 0.f, mlp_zhi = 0.f;
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -182,7 +188,14 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
         int r = ensure_partials(c, (size_t)ns * nseg * 8);
         if (r) return r;
         a.partials = c->d_partials;
-        CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+        if (c->mlp && limit && M >= 0.0) {
+            a.mlp = c->mlp;
+            a.mlp_zlo = c->mlp_zlo;
+            a.mlp_zhi = c->mlp_zhi;
+            CK(crk::step2d_euler_f32_mlp(c->k, c->basis, a, c->wpb, c->stream));
+        } else {
+            CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+        }
     } else {
         const int warps = (c->mesh.nx + 29) / 30;
         const int blocks = (warps + 7) / 8;
@@ -588,6 +601,41 @@ int crkdg_positivity(crkdg_ctx* c, double eps) {
     } else {
         c->pp_eps = 0.0;
     }
+    return CRKDG_OK;
+}
+
+int crkdg_set_indicator(crkdg_ctx* c, const crkdg_mlp* net, double z_lo, double z_hi) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (!net) {
+        c->mlp = nullptr;
+        return CRKDG_OK;
+    }
+    if (c->dim != 2 || c->physics != CRKDG_EULER || c->precision != CRKDG_F32 || c->k != 2)
+        return fail(CRKDG_EUNSUPPORTED, "the learned indicator is built for 2D Euler, k = 2, FP32");
+    if (!(z_lo <= z_hi)) return fail(CRKDG_EINVAL, "need z_lo <= z_hi");
+    c->mlp = crkdg_mlp_device_params(net);
+    c->mlp_zlo = (float)z_lo;
+    c->mlp_zhi = (float)z_hi;
+    return CRKDG_OK;
+}
+
+int crkdg_features(crkdg_ctx* c, float* X_dev, float* y_dev, double M) {
+    if (check_ctx(c) || !X_dev || !y_dev) return fail(CRKDG_EINVAL, "null argument");
+    if (c->dim != 2 || c->physics != CRKDG_EULER || c->precision == CRKDG_F32C)
+        return fail(CRKDG_EUNSUPPORTED, "features are built for 2D Euler FP32/FP64 states");
+    if (!(M >= 0.0)) return fail(CRKDG_EINVAL, "M must be >= 0");
+    if (!c->t_known) {
+        CK(cudaMemcpyAsync(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->t_known = true;
+    }
+    StepArgs a = base_args(c);
+    a.t = c->t;
+    a.M = M;
+    const double h = std::max(dx_of(c), dy_of(c));
+    int r = crkdg_features_impl(a, c->precision, c->k, c->basis, c->u[c->cur], X_dev, y_dev, M * h * h, c->stream);
+    if (r) return fail(r, crkdg_mlp_last_error());
+    CK(cudaStreamSynchronize(c->stream));
     return CRKDG_OK;
 }
 

@@ -16,6 +16,10 @@
 #include "launch.h"
 #include "step2d.cuh"
 
+int crkdg_features_impl(const crk::StepArgs& a, int precision, int k, int basis, const void* u, float* X, float* y,
+                        double Mh2, cudaStream_t st);
+extern "C" const char* crkdg_mlp_last_error(void);
+
 using crk::BatchProblem;
 using crk::DevState;
 using crk::StepArgs;
@@ -380,6 +384,25 @@ int crkdg_batch_get_state(crkdg_batch* b, int p, double* h) {
         BCK(cudaMemcpy(f.data(), base, n * 4, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < n; ++i) h[i] = f[i];
     }
+    return CRKDG_OK;
+}
+
+int crkdg_batch_features(crkdg_batch* b, int p, float* X_dev, float* y_dev, double M) {
+    if (!b || !X_dev || !y_dev || p < 0 || p >= b->n || !(M >= 0.0)) return bfail(CRKDG_EINVAL, "bad argument");
+    int cur = 0;
+    int r = get_cur(b, p, &cur);
+    if (r) return r;
+    const BatchProblem& pb = b->probs[p];
+    StepArgs a = problem_args(b, p);
+    DevState ds;
+    BCK(cudaMemcpy(&ds, b->d_states + p, sizeof(ds), cudaMemcpyDeviceToHost));
+    a.t = ds.t;
+    a.M = M;
+    const double h = std::max(pb.dx, pb.dy);
+    const char* base = static_cast<const char*>(b->buf[cur]) + pb.offset * b->esize;
+    r = crkdg_features_impl(a, b->precision, b->k, b->basis, base, X_dev, y_dev, M * h * h, b->stream);
+    if (r) return bfail(r, crkdg_mlp_last_error());
+    BCK(cudaStreamSynchronize(b->stream));
     return CRKDG_OK;
 }
 

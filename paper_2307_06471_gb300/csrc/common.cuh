@@ -51,6 +51,8 @@ struct StepArgs {
     double pp_eps;            // > 0: positivity-preserving scaling with this floor
     double gamma;
     double beta[2];
+    const float* mlp;         // learned indicator parameters (device), or null
+    float mlp_zlo, mlp_zhi;   // logit band in which the TVB test decides
 };
 
 // -------------------------------------------------------------------------

@@ -45,6 +45,9 @@ cudaError_t project2d_euler_f32c(int k, int basis, const double* vals, void* u, 
 cudaError_t reduce_euler_f32c(const void* u, int nx, int ny, int nm, double dx, double dy, double gamma, DevState* ds,
                               double* partials, int blocks, int set_dt, cudaStream_t st);
 
+// FP32 2D Euler k = 2 step with the fused learned indicator
+cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+
 struct BatchProblem;
 #define CRK_DECL_B(NAME)                                                                                     \
     cudaError_t batch2d_##NAME(int k, int basis, const StepArgs& a, const BatchProblem* probs, const int2* tasks, \

@@ -81,9 +81,12 @@ __device__ __forceinline__ void euler_eig(const T* u, T gamma, T R[4][4], T L[4]
 
 // Limit one cell in place.  u[v][m] modal coefficients, nb* neighbour
 // averages.  Returns true if the cell was troubled.
+// mode -1: the TVB test decides; 0: leave the cell; 1: limit it (slopes
+// become the modified-minmod values, higher modes 0) -- modes 0 and 1 carry
+// the decision of a learned indicator.
 template <class T, int NV, int NM>
 __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, const T* nbE, const T* nbS,
-                                               const T* nbN, T Mdx2, T Mdy2, T gamma) {
+                                               const T* nbN, T Mdx2, T Mdy2, T gamma, int mode = -1) {
     if (NM < 3) return false;
     T avg[NV];
 #pragma unroll
@@ -152,6 +155,7 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
             flag |= (mx[v] != u[v][1]) || (my[v] != u[v][2]);
         }
     }
+    if (mode >= 0) flag = mode == 1;
     if (flag) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {

@@ -23,6 +23,7 @@
 #pragma once
 #include "common.cuh"
 #include "limiter.cuh"
+#include "mlp_warp.cuh"
 
 namespace crk {
 
@@ -64,7 +65,20 @@ struct ProbView {
 // final update u^{n+1} = u^n + Delta is accumulated exactly (TwoSum of hi and
 // Delta + lo), so the state does not collect one rounding of its own size
 // per step.  Used without limiters.
-template <class T, int K, int B, int PHYS, bool COMP = false>
+// MLPI = true: the troubled-cell decision of the limit-on-load comes from the
+// learned indicator (BF16 tensor-core MLP over the warp's 32 cells): limit if
+// the logit exceeds mlp_zhi, keep if it is below mlp_zlo, and let the TVB test
+// decide in between.  The weights sit in shared memory after the threads'
+// private slots, followed by one staging area per warp.
+template <class T, int K, int B, int PHYS>
+__host__ __device__ constexpr size_t mlp_smem_offset(int s, int nthr) {
+    return ((size_t)Step2D<T, K, B, PHYS>::smem_per_thread(s) * sizeof(T) * nthr + 15) / 16 * 16;
+}
+constexpr size_t mlp_smem_bytes(int nthr) {
+    return sizeof(MlpSmem) + (size_t)(nthr / 32) * (32 * MLP_INP + 64) * sizeof(__nv_bfloat16);
+}
+
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false>
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>& pv, const int gw) {
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
@@ -210,7 +224,21 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
             if (!perx && col == nx - 1) load_avg_x(nx, ry_, nbE);
             const bool real = perx ? true : (col >= 0 && col < nx);
             bool fl = false;
-            if (real && a.M >= 0.0) fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam);
+            int mode = -1;
+            if constexpr (MLPI) {
+                // every lane takes part in the warp's MLP evaluation
+                unsigned char* base = smem_raw + mlp_smem_offset<T, K, B, PHYS>(S, nthr);
+                const MlpSmem& mw = *reinterpret_cast<const MlpSmem*>(base);
+                __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(base + sizeof(MlpSmem)) +
+                                       (tid >> 5) * (32 * MLP_INP + 64);
+                float feat[MLP_IN];
+                const double hh = pv.dx > pv.dy ? pv.dx : pv.dy;
+                mlp_features<T, NM>(un, nbE, nbW, avg_next, avg_prev, a.M * hh * hh, feat);
+                const float z = mlp_warp_logit(mw, feat, stage);
+                mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
+            }
+            if (real && a.M >= 0.0)
+                fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam, mode);
             if (real && a.pp_eps > 0.0) positivity_cell<T, NV, NM, K, B>(un, gam, T(a.pp_eps));
             if (out_row && outlane && fl) ++red_trouble;
 #pragma unroll
@@ -571,8 +599,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
 
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
-template <class T, int K, int B, int PHYS, bool COMP = false>
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false>
 __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
+    if constexpr (MLPI) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        MlpSmem& mw = *reinterpret_cast<MlpSmem*>(smem_raw + mlp_smem_offset<T, K, B, PHYS>(a.s, blockDim.x));
+        mlp_load_smem(mw, a.mlp);
+        __syncthreads();
+    }
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
     ProbView<T> pv;
@@ -595,7 +629,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
     pv.cur = nullptr;
     pv.done = nullptr;
     pv.copy_if_idle = 1;
-    step2d_body<T, K, B, PHYS, COMP>(a, pv, gw);
+    step2d_body<T, K, B, PHYS, COMP, MLPI>(a, pv, gw);
 }
 
 // Batched ensemble: problems of different sizes and domains share the

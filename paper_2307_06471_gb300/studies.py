@@ -6,6 +6,10 @@ paper_2307_06471_gb300.studies <name>): each prints one JSON line.
             FP64): DOF-updates/s of the batched, graph-replayed steps
   vortex    isentropic vortex, Q^2, RK4, CFL 0.1, periodic [0,10]^2, to T:
             density L1 error, order over the sizes, FP64 total drift, time
+  learned   learned troubled-cell indicator: labels from ensemble runs,
+            training with the library's kernels, evaluation on the
+            shock-vortex problem (miss / false-flag rates against TVB, L1 vs an
+            FP64 TVB run, DOF-updates/s with and without the network)
 """
 import argparse
 import json
@@ -127,9 +131,134 @@ def ensemble(n=256, steps=40, precision="f32", seed=20230713, autotune=True):
     return out
 
 
+# -- learned troubled-cell indicator ----------------------------------------------------------
+def _shock_vortex_solver(B, GTB, inp, nx, ny, precision, stream):
+    st_up = inp.conserved(1.0, 1.1 * math.sqrt(1.4), 0.0, 1.0)
+    mesh = B.make_mesh(2, nx, ny, (0.0, 2.0, 0.0, 1.0), [B.BC_DIRICHLET, B.BC_OUTFLOW, B.BC_OUTFLOW, B.BC_OUTFLOW],
+                       [B.FN_CONST, 0, 0, 0], [list(st_up), None, None, None])
+    s = B.Solver(mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, precision, stream=stream)
+    s.project_function(lambda X, Y: inp.shock_vortex(X, Y))
+    s.limit(50.0)
+    s.positivity(1e-10)
+    return s
+
+
+def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n=(512, 256), T=0.35,
+            perf_n=(2048, 2048), perf_steps=100, seed=20230713):
+    import torch
+    import crkdg_inputs as inp
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+    M = 50.0
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    out = {"study": "learned", "M": M}
+    # 1. labels from batched runs of the method itself (config-4 ensemble)
+    ens = inp.riemann_ensemble(256, seed=seed)
+    bt = B.Batch([(e["N"], e["N"], (0.0, 1.0, 0.0, 1.0)) for e in ens], 2, B.BASIS_P, GTB.SSPRK3, B.F32, stream=sh)
+    for i, e in enumerate(ens):
+        bt.project_function(i, lambda X, Y: inp.riemann_ic(X, Y, e["prim"]))
+    bt.limit(M)
+    bt.positivity(1e-10)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    feats = {"train": [], "val": []}
+    labels = {"train": [], "val": []}
+    for snap in range(snapshots):
+        bt.run(0.16, 0.2, steps_per_graph=steps_between, max_graphs=1)
+        for i, e in enumerate(ens):
+            n = e["N"] * e["N"]
+            X = torch.empty(n, 40, device="cuda")
+            y = torch.empty(n, device="cuda")
+            bt.features(i, X.data_ptr(), y.data_ptr(), M)
+            keep = (y > 0.5) | (torch.rand(n, device="cuda", generator=g) < 0.05)   # all positives, 5 % negatives
+            part = "train" if i < n_train_members else "val"
+            feats[part].append(X[keep])
+            labels[part].append(y[keep])
+    bt.close()
+    Xtr, ytr = torch.cat(feats["train"]).contiguous(), torch.cat(labels["train"]).contiguous()
+    Xva, yva = torch.cat(feats["val"]).contiguous(), torch.cat(labels["val"]).contiguous()
+    npos = float(ytr.sum().item())
+    pw = (len(ytr) - npos) / max(npos, 1.0)
+    out["train_samples"] = len(ytr)
+    out["train_positive_frac"] = npos / len(ytr)
+    # 2. training with the library's kernels
+    net = B.MLP(seed=1, stream=sh)
+    t0 = time.perf_counter()
+    loss = net.train(Xtr.data_ptr(), ytr.data_ptr(), len(ytr), epochs=epochs, batch=1024, lr=1e-3, pos_weight=pw,
+                     seed=7)
+    out["train_seconds"] = time.perf_counter() - t0
+    out["final_train_loss"] = loss
+    zva = torch.empty(len(yva), device="cuda")
+    net.predict(Xva.data_ptr(), len(yva), zva.data_ptr())
+    pred = zva > 0
+    pos = yva > 0.5
+    out["val_miss_rate_subsampled"] = float((pos & ~pred).sum() / max(pos.sum(), 1))
+    out["val_false_rate_subsampled"] = float((~pos & pred).sum() / max((~pos).sum(), 1))
+    # 3. shock-vortex evaluation (config 5), FP64 TVB reference
+    nx, ny = eval_n
+    runs = {}
+    for name, prec, use_net in (("f64_tvb", B.F64, False), ("f32_tvb", B.F32, False), ("f32_mlp", B.F32, True)):
+        s = _shock_vortex_solver(B, GTB, inp, nx, ny, prec, sh)
+        if use_net:
+            s.set_indicator(net)
+        steps = 0
+        while s.time() < T * (1 - 1e-12):
+            s.advance(100, 0.16, T)
+            steps += 100
+        runs[name] = (s.get_state(), s.sync()[1], steps)
+        if use_net:
+            # rates over every cell of the final state: TVB label vs network decision
+            n = nx * ny
+            X = torch.empty(n, 40, device="cuda")
+            y = torch.empty(n, device="cuda")
+            s.features(X.data_ptr(), y.data_ptr(), M)
+            z = torch.empty(n, device="cuda")
+            net.predict(X.data_ptr(), n, z.data_ptr())
+            lab = y > 0.5
+            prd = z > 0
+            band = (z > -1.3862943611198906) & (z < 1.3862943611198906)
+            out["eval_tvb_flagged"] = int(lab.sum())
+            out["eval_miss_rate"] = float((lab & ~prd).sum() / max(lab.sum(), 1))
+            out["eval_false_rate"] = float((~lab & prd).sum() / max((~lab).sum(), 1))
+            out["eval_band_fallback_frac"] = float(band.float().mean())
+        s.close()
+    ref = runs["f64_tvb"][0][0, 0]
+    cells = nx * ny
+    for name in ("f32_tvb", "f32_mlp"):
+        out["L1_density_vs_f64_tvb_" + name] = float(np.abs(runs[name][0][0, 0] - ref).sum() / cells)
+        out["status_" + name] = runs[name][1]
+    out["eval_mesh"] = "%dx%d" % eval_n
+    out["T"] = T
+    # 4. throughput at 2048 x 2048 (device steps, L2 not a factor at 403 MB)
+    nx, ny = perf_n
+    for name, prec, use_net in (("f32_tvb", B.F32, False), ("f32_mlp", B.F32, True), ("f64_tvb", B.F64, False)):
+        s = _shock_vortex_solver(B, GTB, inp, nx, ny, prec, sh)
+        if use_net:
+            s.set_indicator(net)
+        n_steps = perf_steps if prec == B.F32 else max(5, perf_steps // 10)
+        s.advance(3, 0.16, 10.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            s.step_device()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n_steps
+        out["dof_per_s_" + name] = nx * ny * 24 / (ms * 1e-3)
+        out["ms_per_step_" + name] = ms
+        s.close()
+    out["perf_mesh"] = "%dx%d" % perf_n
+    net.close()
+    return out
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["vortex", "ensemble"])
+    ap.add_argument("study", choices=["vortex", "ensemble", "learned"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -138,6 +267,8 @@ if __name__ == "__main__":
     a = ap.parse_args()
     if a.study == "vortex":
         r = vortex(tuple(int(x) for x in a.sizes.split(",")), a.T, a.precision)
+    elif a.study == "learned":
+        r = learned()
     else:
         r = ensemble(a.n, a.steps, a.precision)
     print(json.dumps(r, default=float))
