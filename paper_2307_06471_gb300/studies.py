@@ -144,7 +144,7 @@ def _shock_vortex_solver(B, GTB, inp, nx, ny, precision, stream):
 
 
 def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n=(512, 256), T=0.35,
-            perf_n=(2048, 2048), perf_steps=100, seed=20230713):
+            perf_n=(2048, 2048), perf_steps=100, seed=20230713, pos_weights=None):
     import torch
     import crkdg_inputs as inp
     from paper_2307_06471_gb300 import binding as B
@@ -181,57 +181,62 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
     Xtr, ytr = torch.cat(feats["train"]).contiguous(), torch.cat(labels["train"]).contiguous()
     Xva, yva = torch.cat(feats["val"]).contiguous(), torch.cat(labels["val"]).contiguous()
     npos = float(ytr.sum().item())
-    pw = (len(ytr) - npos) / max(npos, 1.0)
     out["train_samples"] = len(ytr)
     out["train_positive_frac"] = npos / len(ytr)
-    # 2. training with the library's kernels
-    net = B.MLP(seed=1, stream=sh)
-    t0 = time.perf_counter()
-    loss = net.train(Xtr.data_ptr(), ytr.data_ptr(), len(ytr), epochs=epochs, batch=1024, lr=1e-3, pos_weight=pw,
-                     seed=7)
-    out["train_seconds"] = time.perf_counter() - t0
-    out["final_train_loss"] = loss
-    zva = torch.empty(len(yva), device="cuda")
-    net.predict(Xva.data_ptr(), len(yva), zva.data_ptr())
-    pred = zva > 0
-    pos = yva > 0.5
-    out["val_miss_rate_subsampled"] = float((pos & ~pred).sum() / max(pos.sum(), 1))
-    out["val_false_rate_subsampled"] = float((~pos & pred).sum() / max((~pos).sum(), 1))
-    # 3. shock-vortex evaluation (config 5), FP64 TVB reference
+    out["negative_keep_frac"] = 0.05
+    # 3. shock-vortex evaluation (config 5): FP64 TVB reference and FP32 TVB once
     nx, ny = eval_n
-    runs = {}
-    for name, prec, use_net in (("f64_tvb", B.F64, False), ("f32_tvb", B.F32, False), ("f32_mlp", B.F32, True)):
+
+    def run(prec, net=None):
         s = _shock_vortex_solver(B, GTB, inp, nx, ny, prec, sh)
-        if use_net:
+        if net is not None:
             s.set_indicator(net)
-        steps = 0
         while s.time() < T * (1 - 1e-12):
             s.advance(100, 0.16, T)
-            steps += 100
-        runs[name] = (s.get_state(), s.sync()[1], steps)
-        if use_net:
-            # rates over every cell of the final state: TVB label vs network decision
+        res = {"state": s.get_state(), "status": s.sync()[1]}
+        if net is not None:
             n = nx * ny
             X = torch.empty(n, 40, device="cuda")
             y = torch.empty(n, device="cuda")
             s.features(X.data_ptr(), y.data_ptr(), M)
             z = torch.empty(n, device="cuda")
             net.predict(X.data_ptr(), n, z.data_ptr())
-            lab = y > 0.5
-            prd = z > 0
+            lab, prd = y > 0.5, z > 0
             band = (z > -1.3862943611198906) & (z < 1.3862943611198906)
-            out["eval_tvb_flagged"] = int(lab.sum())
-            out["eval_miss_rate"] = float((lab & ~prd).sum() / max(lab.sum(), 1))
-            out["eval_false_rate"] = float((~lab & prd).sum() / max((~lab).sum(), 1))
-            out["eval_band_fallback_frac"] = float(band.float().mean())
+            res.update(tvb_flagged=int(lab.sum()), miss=float((lab & ~prd).sum() / max(lab.sum(), 1)),
+                       false=float((~lab & prd).sum() / max((~lab).sum(), 1)), band=float(band.float().mean()))
         s.close()
-    ref = runs["f64_tvb"][0][0, 0]
+        return res
+
+    ref = run(B.F64)["state"][0, 0]
     cells = nx * ny
-    for name in ("f32_tvb", "f32_mlp"):
-        out["L1_density_vs_f64_tvb_" + name] = float(np.abs(runs[name][0][0, 0] - ref).sum() / cells)
-        out["status_" + name] = runs[name][1]
+    tvb32 = run(B.F32)
+    out["L1_density_f32_tvb"] = float(np.abs(tvb32["state"][0, 0] - ref).sum() / cells)
     out["eval_mesh"] = "%dx%d" % eval_n
     out["T"] = T
+    # 2. training with the library's kernels, one network per class weight
+    # (pos_weight = keep fraction restores the natural class prior; 1.0 and
+    # the balanced weight over-weight positives)
+    nets = []
+    out["networks"] = []
+    for pw in pos_weights if pos_weights else (0.05, 0.25, (len(ytr) - npos) / max(npos, 1.0)):
+        net = B.MLP(seed=1, stream=sh)
+        t0 = time.perf_counter()
+        loss = net.train(Xtr.data_ptr(), ytr.data_ptr(), len(ytr), epochs=epochs, batch=1024, lr=1e-3, pos_weight=pw,
+                         seed=7)
+        row = {"pos_weight": pw, "train_seconds": time.perf_counter() - t0, "final_train_loss": loss}
+        zva = torch.empty(len(yva), device="cuda")
+        net.predict(Xva.data_ptr(), len(yva), zva.data_ptr())
+        pred, pos = zva > 0, yva > 0.5
+        row["val_miss_rate_subsampled"] = float((pos & ~pred).sum() / max(pos.sum(), 1))
+        row["val_false_rate_subsampled"] = float((~pos & pred).sum() / max((~pos).sum(), 1))
+        r = run(B.F32, net)
+        row.update(eval_miss_rate=r["miss"], eval_false_rate=r["false"], eval_band_fallback_frac=r["band"],
+                   eval_tvb_flagged=r["tvb_flagged"], status=r["status"],
+                   L1_density=float(np.abs(r["state"][0, 0] - ref).sum() / cells))
+        out["networks"].append(row)
+        nets.append(net)
+    net = nets[0]
     # 4. throughput at 2048 x 2048 (device steps, L2 not a factor at 403 MB)
     nx, ny = perf_n
     for name, prec, use_net in (("f32_tvb", B.F32, False), ("f32_mlp", B.F32, True), ("f64_tvb", B.F64, False)):
@@ -252,7 +257,8 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
         out["ms_per_step_" + name] = ms
         s.close()
     out["perf_mesh"] = "%dx%d" % perf_n
-    net.close()
+    for n_ in nets:
+        n_.close()
     return out
 
 
