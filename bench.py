@@ -207,6 +207,24 @@ def dist_init():
     return rank, ws
 
 
+def aggregate(dev_ms, dof_per_rank, steps):
+    """Whole-job figures of N independent replicas: the slowest rank's device
+    time (max over ranks) and value = N * DOF * steps / that time."""
+    ws = 1
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            import torch
+            ws = dist.get_world_size()
+            dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+            t = torch.tensor([float(dev_ms)], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dev_ms = float(t.item())
+    except ImportError:
+        pass
+    return dev_ms, ws * dof_per_rank * steps / (dev_ms * 1e-3), ws
+
+
 def run_reference(args):
     rank, ws = dist_init()
     if rank != 0:
@@ -286,12 +304,8 @@ def main():
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     code, status = s.sync()
     t_sim = s.time()
-    ms = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
-    dev_ms = float(ms.item())
+    dev_ms, value, _ = aggregate(dev_ms, dof, args.steps)
     ms_per_step = dev_ms / args.steps
-    value = ws * dof * args.steps / (dev_ms * 1e-3)
 
     A, b = GTB.BY_NAME[WL["tab"]]
     fpc = step_flops_per_cell(WL["k"], WL["basis"], "euler", A, b, limiter=True)

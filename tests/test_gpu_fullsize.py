@@ -1,0 +1,107 @@
+"""Parity at the full bench size (DMR 1920 x 480, P^2, SSP-RK3, TVB M = 50 +
+positivity) in the launch configuration bench.py times.  The oracle cannot
+run the full mesh, so sampled cells are recomputed one by one: a cRKDG step
+with end-of-step limiting depends on the cell's neighbours up to distance 3
+(limit u^n: averages at distance 2 for the neighbours' limiting; limit
+u^{n+1}: the neighbours' new averages), so the oracle steps a 7 x 7 patch
+around each sampled cell, with the domain's boundary conditions on the sides
+the patch shares with the domain, and the centre cell is compared."""
+import numpy as np
+import pytest
+
+import crkdg_inputs as inp
+from oracle import tableaux as OTB
+from oracle.dg2d import DG2D, crkdg_step
+from oracle.limiter import positivity_limit, tvb_limit
+from oracle.physics import Euler
+from tests.pairing import oracle_bc
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, BOX = 1920, 480, (0.0, 4.0, 0.0, 1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_06471_gb300 import build
+    build.build()
+
+
+def _bcs():
+    st = inp.dmr_states()
+    post, pre = list(st["post"]), list(st["pre"])
+    return {"W": ("const", post), "E": ("outflow",), "S": ("dmr_bottom", post, st["x0"]),
+            "N": ("dmr_top", post, pre, st["x0"], st["slope"], st["xspeed"])}
+
+
+def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10):
+    """u: full state [y, x, v, m] (FP64 values of the GPU input); returns the
+    oracle's limited u^{n+1} of cell (y, x)."""
+    dx, dy = (BOX[1] - BOX[0]) / NX, (BOX[3] - BOX[2]) / NY
+    ya, yb = max(0, y - 3), min(NY, y + 4)
+    xa, xb = max(0, x - 3), min(NX, x + 4)
+    bcs = _bcs()
+    side = {"W": xa == 0, "E": xb == NX, "S": ya == 0, "N": yb == NY}
+    obc = {s: (oracle_bc(bcs[s], 0 if s in "WE" else 1) if side[s] else "outflow") for s in "WESN"}
+    box = (BOX[0] + xa * dx, BOX[0] + xb * dx, BOX[2] + ya * dy, BOX[2] + yb * dy)
+    dg = DG2D(xb - xa, yb - ya, box, 2, "P", Euler(1.4, 2), obc)
+    lim = lambda v, t: positivity_limit(dg, tvb_limit(dg, v, M, t)[0], eps)
+    p = u[ya:yb, xa:xb]
+    w = crkdg_step(dg, lim(p, t0), t0, dt, OTB.SSPRK3, limiter=lim)
+    return w[y - ya, x - xa]
+
+
+def _samples(rng, n_interior):
+    cells = [(0, 5), (0, 700), (NY - 1, 300), (NY - 1, 1500), (200, 0), (100, NX - 1), (0, 0), (NY - 1, NX - 1)]
+    while len(cells) < 8 + n_interior:
+        cells.append((int(rng.integers(0, NY)), int(rng.integers(0, 400))))   # the active region near the shock
+    return cells
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_size_dmr_sampled_cells(prec):
+    import torch
+    import bench
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    stream = torch.cuda.Stream()
+    st = inp.dmr_states()
+    mesh, _ = bench.dmr_mesh(B, inp, NX, NY)
+    s = B.Solver(mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F64 if prec == "f64" else B.F32, stream=stream.cuda_stream)
+    assert s.get_launch() == (26, 4)                   # the launch shape bench.py times
+    s.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    s.limit(50.0)
+    s.positivity(1e-10)
+    s.advance(20, 0.16, 0.2)                           # a developed state
+    # u^n: the stored state without its pending limit (saved raw), and t^n
+    u_raw = None
+    import os
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        s.save(path)
+        raw = np.fromfile(path, dtype=np.uint8)
+    hdr = np.frombuffer(raw[:32].tobytes(), dtype=np.int32)
+    dh = np.frombuffer(raw[32:80].tobytes(), dtype=np.float64)
+    u_raw = np.frombuffer(raw[80:].tobytes(), dtype=np.float64).reshape(4, 6, NY, NX)
+    t0 = dh[0]
+    assert hdr[0] == 0x43524B44 and dh[1] == 1.0        # pending limit recorded
+    s.step_device()
+    t1 = s.time()
+    got = np.transpose(s.get_state(), (2, 3, 0, 1))
+    code, status = s.sync()
+    assert code == 0 and status == 0
+    u = np.transpose(u_raw, (2, 3, 0, 1))
+    rng = np.random.default_rng(2024)
+    bad = []
+    for (y, x) in _samples(rng, 24):
+        want = _oracle_cell(u, y, x, t0, t1 - t0)
+        err = np.max(np.abs(got[y, x] - want)) / max(1.0, np.max(np.abs(want)))
+        tol = 1e-12 if prec == "f64" else 2e-5
+        if not err < tol:
+            bad.append((y, x, err))
+    if prec == "f64":
+        assert not bad, bad
+    else:
+        # FP32 limiter decisions may differ from FP64 ones at exact ties only
+        assert len(bad) <= 1, bad

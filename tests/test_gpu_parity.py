@@ -316,3 +316,34 @@ def test_compensated_state_tracks_fp64_over_many_steps():
     assert e32c < 1e-6
     assert e32c < 0.2 * e32
     assert np.max(res["f32c"][1]) < 0.5 * np.max(res["f32"][1])
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    """save after 5 steps, continue 5 steps; a fresh context loaded from the
+    checkpoint and stepped 5 times gives the same bits (pending limit, t and
+    limiter settings travel with the checkpoint)."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    bcs, st = _dmr_bcs()
+    stream = torch.cuda.Stream()
+
+    def fresh():
+        gs, dg = make_pair_2d(96, 24, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, "f32")
+        gs.close()
+        return B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32, stream=stream.cuda_stream)
+
+    a = fresh()
+    a.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    a.limit(50.0)
+    a.positivity(1e-10)
+    a.advance(5, 0.16, 0.2)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.advance(5, 0.16, 0.2)
+    want, t_want = a.get_state(), a.time()
+    b = fresh()
+    b.load(path)
+    b.advance(5, 0.16, 0.2)
+    assert np.array_equal(b.get_state(), want)
+    assert b.time() == t_want
