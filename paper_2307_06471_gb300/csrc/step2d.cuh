@@ -27,6 +27,20 @@
 
 namespace crk {
 
+// a0 += x0 * c, a1 += x1 * c: one packed FP32x2 FMA on sm_100+ for float
+// (the same fused rounding as two scalar FMAs), two FMAs for double
+template <class T>
+__device__ __forceinline__ void pfma(T& a0, T& a1, T x0, T x1, T c) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = __ffma2_rn(make_float2(x0, x1), make_float2(c, c), make_float2(a0, a1));
+        a0 = r.x;
+        a1 = r.y;
+    } else {
+        a0 = fma(x0, c, a0);
+        a1 = fma(x1, c, a1);
+    }
+}
+
 template <class T, int K, int B, int PHYS>
 struct Step2D {
     using TB = Tab2D<K, B>;
@@ -43,21 +57,65 @@ struct Step2D {
     }
 };
 
-// Per-problem view of one step: the single-problem kernel builds it from
-// its launch arguments, the batched kernel from the problem table.
+// Per-problem view of one step.  The single-problem kernel reads the mesh
+// straight from its launch arguments (kernel-parameter constant bank, no
+// registers held); the batched kernel reads it from the problem table.
+template <class T>
+struct ArgsView {
+    const StepArgs& a;
+    double t_, dt_;
+    __device__ __forceinline__ const T* uin() const { return static_cast<const T*>(a.uin); }
+    __device__ __forceinline__ T* uout() const { return static_cast<T*>(a.uout); }
+    __device__ __forceinline__ int nx() const { return a.nx; }
+    __device__ __forceinline__ int ny() const { return a.ny; }
+    __device__ __forceinline__ double x0() const { return a.x0; }
+    __device__ __forceinline__ double y0() const { return a.y0; }
+    __device__ __forceinline__ double dx() const { return a.dx; }
+    __device__ __forceinline__ double dy() const { return a.dy; }
+    __device__ __forceinline__ double t() const { return t_; }
+    __device__ __forceinline__ double dt() const { return dt_; }
+    __device__ __forceinline__ int n_strips() const { return a.n_strips; }
+    __device__ __forceinline__ int n_segs() const { return a.n_segs; }
+    __device__ __forceinline__ int seg_len() const { return a.seg_len; }
+    __device__ __forceinline__ int total_warps() const { return a.n_strips * a.n_segs; }
+    __device__ __forceinline__ double* partials() const { return a.partials; }
+    __device__ __forceinline__ DevState* ds() const { return a.ds; }
+    __device__ __forceinline__ int* cur() const { return nullptr; }
+    __device__ __forceinline__ unsigned* done() const { return nullptr; }
+    __device__ __forceinline__ bool copy_if_idle() const { return true; }
+};
+
 template <class T>
 struct ProbView {
-    const T* uin;
-    T* uout;
-    int nx, ny;
-    double x0, y0, dx, dy;
-    double t, dt;
-    int n_strips, n_segs, seg_len, total_warps;
-    double* partials;     // this problem's per-warp reduction slots
-    DevState* ds;         // this problem's run state
-    int* cur;             // batched runs: this problem's buffer index (flipped by its last warp)
-    unsigned* done;       // batched runs: count of problems that reached t_end
-    int copy_if_idle;     // single-problem runs copy u^n when dt <= 0
+    const T* uin_;
+    T* uout_;
+    int nx_, ny_;
+    double x0_, y0_, dx_, dy_;
+    double t_, dt_;
+    int n_strips_, n_segs_, seg_len_, total_warps_;
+    double* partials_;    // this problem's per-warp reduction slots
+    DevState* ds_;        // this problem's run state
+    int* cur_;            // this problem's buffer index (flipped by its last warp)
+    unsigned* done_;      // count of problems that reached t_end
+    __device__ __forceinline__ const T* uin() const { return uin_; }
+    __device__ __forceinline__ T* uout() const { return uout_; }
+    __device__ __forceinline__ int nx() const { return nx_; }
+    __device__ __forceinline__ int ny() const { return ny_; }
+    __device__ __forceinline__ double x0() const { return x0_; }
+    __device__ __forceinline__ double y0() const { return y0_; }
+    __device__ __forceinline__ double dx() const { return dx_; }
+    __device__ __forceinline__ double dy() const { return dy_; }
+    __device__ __forceinline__ double t() const { return t_; }
+    __device__ __forceinline__ double dt() const { return dt_; }
+    __device__ __forceinline__ int n_strips() const { return n_strips_; }
+    __device__ __forceinline__ int n_segs() const { return n_segs_; }
+    __device__ __forceinline__ int seg_len() const { return seg_len_; }
+    __device__ __forceinline__ int total_warps() const { return total_warps_; }
+    __device__ __forceinline__ double* partials() const { return partials_; }
+    __device__ __forceinline__ DevState* ds() const { return ds_; }
+    __device__ __forceinline__ int* cur() const { return cur_; }
+    __device__ __forceinline__ unsigned* done() const { return done_; }
+    __device__ __forceinline__ bool copy_if_idle() const { return false; }
 };
 
 // COMP = true: compensated FP32 state.  The buffers hold hi planes followed
@@ -78,8 +136,8 @@ constexpr size_t mlp_smem_bytes(int nthr) {
     return sizeof(MlpSmem) + (size_t)(nthr / 32) * (32 * MLP_INP + 64) * sizeof(__nv_bfloat16);
 }
 
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false>
-__device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>& pv, const int gw) {
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, class PV>
+__device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
     constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
@@ -95,18 +153,18 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
     auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
 
     const int lane = tid & 31;
-    const int total_warps = pv.total_warps;
+    const int total_warps = pv.total_warps();
 
-    const int nx = pv.nx, ny = pv.ny;
+    const int nx = pv.nx(), ny = pv.ny();
     const size_t plane = (size_t)nx * ny;
-    const T* __restrict__ uin = pv.uin;
-    T* __restrict__ uout = pv.uout;
+    const T* __restrict__ uin = pv.uin();
+    T* __restrict__ uout = pv.uout();
 
-    const double dt = pv.dt;
-    const double t0 = pv.t;
+    const double dt = pv.dt();
+    const double t0 = pv.t();
 
-    const int strip = gw % pv.n_strips;
-    const int seg = gw / pv.n_strips;
+    const int strip = gw % pv.n_strips();
+    const int seg = gw / pv.n_strips();
     const int xs = strip * 30;
     const int col = xs - 1 + lane;
     const bool perx = a.bc[0].type == BC_PERIODIC;
@@ -117,14 +175,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
     const bool has_bcW = !perx && xs == 0;
     const bool has_bcE = !perx && xs + 30 >= nx;
 
-    const int r0 = seg * pv.seg_len;
-    const int r1 = min(r0 + pv.seg_len, ny);
+    const int r0 = seg * pv.seg_len();
+    const int r1 = min(r0 + pv.seg_len(), ny);
     const int rstart = (r0 > 0 || pery) ? r0 - 1 : r0;
     const int rend = (r1 < ny || pery) ? r1 : r1 - 1;
 
     // a non-positive dt leaves the state unchanged (runs past t_end)
     if (!(dt > 0.0)) {
-        if (pv.copy_if_idle && outlane)
+        if (pv.copy_if_idle() && outlane)
             for (int r = r0; r < r1; ++r)
                 for (int d = 0; d < (COMP ? 2 : 1) * C::NDOF; ++d)
                     uout[d * plane + (size_t)r * nx + col] = uin[d * plane + (size_t)r * nx + col];
@@ -139,9 +197,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
         ph.bx = T(a.beta[0]);
         ph.by = T(a.beta[1]);
     }
-    const T rx = T(1.0 / pv.dx), ry = T(1.0 / pv.dy);
+    const T rx = T(1.0 / pv.dx()), ry = T(1.0 / pv.dy());
     const T tdt = T(dt);
-    const T Mdx2 = T(a.M * pv.dx * pv.dx), Mdy2 = T(a.M * pv.dy * pv.dy);
+    const T Mdx2 = T(a.M * pv.dx() * pv.dx()), Mdy2 = T(a.M * pv.dy() * pv.dy());
     const T gam = T(a.gamma);
 
     // reduction accumulators (FP64)
@@ -169,8 +227,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = r < 0 ? 2 : 3;
-            const double xc = pv.x0 + (col + 0.5) * pv.dx;
-            const double yc = r < 0 ? pv.y0 - 0.5 * pv.dy : pv.y0 + (ny + 0.5) * pv.dy;
+            const double xc = pv.x0() + (col + 0.5) * pv.dx();
+            const double yc = r < 0 ? pv.y0() - 0.5 * pv.dy() : pv.y0() + (ny + 0.5) * pv.dy();
             bc_exterior<T, NV>(a.bc[side], 1, own, xc, yc, t0, out);
         }
     };
@@ -185,8 +243,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = c < 0 ? 0 : 1;
-            const double xc = c < 0 ? pv.x0 - 0.5 * pv.dx : pv.x0 + (nx + 0.5) * pv.dx;
-            const double yc = pv.y0 + (r + 0.5) * pv.dy;
+            const double xc = c < 0 ? pv.x0() - 0.5 * pv.dx() : pv.x0() + (nx + 0.5) * pv.dx();
+            const double yc = pv.y0() + (r + 0.5) * pv.dy();
             bc_exterior<T, NV>(a.bc[side], 0, own, xc, yc, t0, out);
         }
     };
@@ -198,7 +256,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
         const bool south_bc = (r == 0) && !pery;
         const bool do_south = (r > rstart) || south_bc;   // flux through this row's south face
         const bool keep_north = r < rend || (r == ny - 1 && !pery && out_row);
-        const double yc = pv.y0 + (ry_ + 0.5) * pv.dy;
+        const double yc = pv.y0() + (ry_ + 0.5) * pv.dy();
 
         // ---- load u^n (and limit on load) -------------------------------------
         T un[NV][NM];
@@ -232,7 +290,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                 __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(base + sizeof(MlpSmem)) +
                                        (tid >> 5) * (32 * MLP_INP + 64);
                 float feat[MLP_IN];
-                const double hh = pv.dx > pv.dy ? pv.dx : pv.dy;
+                const double hh = pv.dx() > pv.dy() ? pv.dx() : pv.dy();
                 mlp_features<T, NM>(un, nbE, nbW, avg_next, avg_prev, a.M * hh * hh, feat);
                 const float z = mlp_warp_logit(mw, feat, stage);
                 mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
@@ -275,10 +333,19 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                 const double aijd = tab_a(a, i, j);
                 if (aijd == 0.0) continue;
                 const T aij = T(aijd) * tdt;
+                if constexpr (NV % 2 == 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v)
+                    for (int v = 0; v < NV; v += 2)
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) w[v][m] -= aij * slot(j * C::NDOF + v * NM + m);
+                        for (int m = 0; m < NM; ++m)
+                            pfma(w[v][m], w[v + 1][m], slot(j * C::NDOF + v * NM + m),
+                                 slot(j * C::NDOF + (v + 1) * NM + m), -aij);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) w[v][m] -= aij * slot(j * C::NDOF + v * NM + m);
+                }
             }
             // volume term  sum_q w_q (rx f_x dphi/dxi + ry f_y dphi/deta)
             T vol[NV][NM];
@@ -289,33 +356,80 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
 #pragma unroll
             for (int q = 0; q < NQV; ++q) {
                 T uq[NV];
+                if constexpr (NV % 2 == 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    T s = T(0);
+                    for (int v = 0; v < NV; v += 2) {
+                        T s0 = T(0), s1 = T(0);
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) s += w[v][m] * T(tb.phi[q][m]);
-                    uq[v] = s;
+                        for (int m = 0; m < NM; ++m) pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
+                        uq[v] = s0;
+                        uq[v + 1] = s1;
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        T s = T(0);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) s += w[v][m] * T(tb.phi[q][m]);
+                        uq[v] = s;
+                    }
                 }
                 T fx[NV], fy[NV];
                 ph.flux2(uq, fx, fy);
+                if constexpr (NV % 2 == 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const T gxv = rx * fx[v], gyv = ry * fy[v];
+                    for (int v = 0; v < NV; v += 2) {
+                        const T gx0 = rx * fx[v], gx1 = rx * fx[v + 1], gy0 = ry * fy[v], gy1 = ry * fy[v + 1];
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) {
-                        if (tb.gx[q][m] != 0.0) vol[v][m] += gxv * T(tb.gx[q][m]);
-                        if (tb.gy[q][m] != 0.0) vol[v][m] += gyv * T(tb.gy[q][m]);
+                        for (int m = 0; m < NM; ++m) {
+                            if (tb.gx[q][m] != 0.0) pfma(vol[v][m], vol[v + 1][m], gx0, gx1, T(tb.gx[q][m]));
+                            if (tb.gy[q][m] != 0.0) pfma(vol[v][m], vol[v + 1][m], gy0, gy1, T(tb.gy[q][m]));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const T gxv = rx * fx[v], gyv = ry * fy[v];
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            if (tb.gx[q][m] != 0.0) vol[v][m] += gxv * T(tb.gx[q][m]);
+                            if (tb.gy[q][m] != 0.0) vol[v][m] += gyv * T(tb.gy[q][m]);
+                        }
                     }
                 }
             }
             if (need_flux && out_row) {
+                if constexpr (NV % 2 == 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v)
+                    for (int v = 0; v < NV; v += 2)
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) V[v][m] += bi * vol[v][m];
+                        for (int m = 0; m < NM; ++m) pfma(V[v][m], V[v + 1][m], vol[v][m], vol[v + 1][m], bi);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) V[v][m] += bi * vol[v][m];
+                }
             }
             // face traces
             T tE[NQ][NV], tW[NQ][NV], tN[NQ][NV], tS[NQ][NV];
+            if constexpr (NV % 2 == 0) {
+#pragma unroll
+                for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                    for (int v = 0; v < NV; v += 2) {
+                        T e0 = 0, e1 = 0, w0 = 0, w1 = 0, n0 = 0, n1 = 0, s0 = 0, s1 = 0;
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            pfma(e0, e1, w[v][m], w[v + 1][m], T(tb.tE[p][m]));
+                            pfma(w0, w1, w[v][m], w[v + 1][m], T(tb.tW[p][m]));
+                            pfma(n0, n1, w[v][m], w[v + 1][m], T(tb.tN[p][m]));
+                            pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.tS[p][m]));
+                        }
+                        tE[p][v] = e0; tE[p][v + 1] = e1; tW[p][v] = w0; tW[p][v + 1] = w1;
+                        tN[p][v] = n0; tN[p][v + 1] = n1; tS[p][v] = s0; tS[p][v + 1] = s1;
+                    }
+            } else {
 #pragma unroll
             for (int p = 0; p < NQ; ++p)
 #pragma unroll
@@ -330,6 +444,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                     }
                     tE[p][v] = e; tW[p][v] = ww; tN[p][v] = n; tS[p][v] = s;
                 }
+            }
             // local operator L_i = cm (face_loc - vol), eq. (2.7)
             if (need_L) {
                 T floc[NV][NM];
@@ -344,12 +459,27 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                     ph.template fluxn<0>(tW[p], fw);
                     ph.template fluxn<1>(tN[p], fn);
                     ph.template fluxn<1>(tS[p], fs);
+                    if constexpr (NV % 2 == 0) {
 #pragma unroll
-                    for (int v = 0; v < NV; ++v)
+                        for (int v = 0; v < NV; v += 2) {
+                            const T ge0 = rx * fe[v], ge1 = rx * fe[v + 1], gw0 = rx * fw[v], gw1 = rx * fw[v + 1];
+                            const T gn0 = ry * fn[v], gn1 = ry * fn[v + 1], gs0 = ry * fs[v], gs1 = ry * fs[v + 1];
 #pragma unroll
-                        for (int m = 0; m < NM; ++m)
-                            floc[v][m] += rx * (fe[v] * T(tb.pE[p][m]) - fw[v] * T(tb.pW[p][m])) +
-                                          ry * (fn[v] * T(tb.pN[p][m]) - fs[v] * T(tb.pS[p][m]));
+                            for (int m = 0; m < NM; ++m) {
+                                if (tb.pE[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], ge0, ge1, T(tb.pE[p][m]));
+                                if (tb.pW[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gw0, gw1, -T(tb.pW[p][m]));
+                                if (tb.pN[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gn0, gn1, T(tb.pN[p][m]));
+                                if (tb.pS[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gs0, gs1, -T(tb.pS[p][m]));
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v)
+#pragma unroll
+                            for (int m = 0; m < NM; ++m)
+                                floc[v][m] += rx * (fe[v] * T(tb.pE[p][m]) - fw[v] * T(tb.pW[p][m])) +
+                                              ry * (fn[v] * T(tb.pN[p][m]) - fs[v] * T(tb.pS[p][m]));
+                    }
                 }
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
@@ -368,12 +498,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                 if (has_bcW && lane == 0) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0, yc + 0.5 * pv.dy * tb.xq[p], ti, tE[p]);
+                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0(), yc + 0.5 * pv.dy() * tb.xq[p], ti, tE[p]);
                 }
                 if (has_bcE && col == nx - 1) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0 + nx * pv.dx, yc + 0.5 * pv.dy * tb.xq[p], ti,
+                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0() + nx * pv.dx(), yc + 0.5 * pv.dy() * tb.xq[p], ti,
                                            tWn[p]);
                 }
 #pragma unroll
@@ -390,8 +520,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                 for (int p = 0; p < NQ; ++p) {
                     T lo[NV];
                     if (south_bc) {
-                        const double xp = pv.x0 + (col + 0.5) * pv.dx + 0.5 * pv.dx * tb.xq[p];
-                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0, ti, lo);
+                        const double xp = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0(), ti, lo);
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
@@ -449,11 +579,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                 const double w = av[1] * ir, vv = av[2] * ir;
                 const double p = (a.gamma - 1.0) * (av[3] - 0.5 * (av[1] * w + av[2] * vv));
                 const double c = sqrt(fmax(a.gamma * p * ir, 0.0));
-                sp = (fabs(w) + c) / pv.dx + (fabs(vv) + c) / pv.dy;
+                sp = (fabs(w) + c) / pv.dx() + (fabs(vv) + c) / pv.dy();
                 if (!(av[0] > 0.0) || !(p > 0.0)) status |= ST_NONPHYSICAL;
                 if (!(sp == sp)) status |= ST_NAN;
             } else {
-                sp = fabs(a.beta[0]) / pv.dx + fabs(a.beta[1]) / pv.dy;
+                sp = fabs(a.beta[0]) / pv.dx() + fabs(a.beta[1]) / pv.dy();
                 if (!(av[0] == av[0])) status |= ST_NAN;
             }
             red_max = fmax(red_max, sp);
@@ -509,8 +639,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
                     T lo[NV], hi[NV], F[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
-                    const double xp = pv.x0 + (col + 0.5) * pv.dx + 0.5 * pv.dx * tb.xq[p];
-                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, pv.y0 + ny * pv.dy, ti, hi);
+                    const double xp = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, pv.y0() + ny * pv.dy(), ti, hi);
                     llf<T, PHYS, 1>(ph, lo, hi, F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FN[p][v] += bi * F[v];
@@ -535,7 +665,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
     }
 
     // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
-    const double cell = pv.dx * pv.dy;
+    const double cell = pv.dx() * pv.dy();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
@@ -544,16 +674,16 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
         red_trouble += __shfl_xor_sync(0xffffffffu, red_trouble, off);
         status |= __shfl_xor_sync(0xffffffffu, status, off);
     }
-    double* slotp = pv.partials + (size_t)gw * C::NRED;
+    double* slotp = pv.partials() + (size_t)gw * C::NRED;
     unsigned prev = 0;
     if (lane == 0) {
         slotp[0] = red_max;
 #pragma unroll
         for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
         slotp[1 + NV] = double(red_trouble);
-        if (status) atomicOr(&pv.ds->status, status);
+        if (status) atomicOr(&pv.ds()->status, status);
         __threadfence();
-        prev = atomicAdd(&pv.ds->counter, 1u);
+        prev = atomicAdd(&pv.ds()->counter, 1u);
     }
     prev = __shfl_sync(0xffffffffu, prev, 0);
     if (prev != (unsigned)total_warps - 1) return;
@@ -563,7 +693,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
     for (int wi = lane; wi < total_warps; wi += 32) {
-        const double* q = pv.partials + (size_t)wi * C::NRED;
+        const double* q = pv.partials() + (size_t)wi * C::NRED;
         mx = fmax(mx, __ldcg(q));
 #pragma unroll
         for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
@@ -577,7 +707,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
         tr += __shfl_xor_sync(0xffffffffu, tr, off);
     }
     if (lane == 0) {
-        DevState* ds = pv.ds;
+        DevState* ds = pv.ds();
         ds->maxspeed = mx;
 #pragma unroll
         for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
@@ -592,8 +722,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const ProbView<T>
         ds->dt = dn;
         ds->steps += 1;
         ds->counter = 0;
-        if (pv.cur) *pv.cur ^= 1;
-        if (pv.done && reached) atomicAdd(pv.done, 1u);
+        if (pv.cur()) *pv.cur() ^= 1;
+        if (pv.done() && reached) atomicAdd(pv.done(), 1u);
     }
 }
 
@@ -609,26 +739,7 @@ __global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
     }
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
-    ProbView<T> pv;
-    pv.uin = static_cast<const T*>(a.uin);
-    pv.uout = static_cast<T*>(a.uout);
-    pv.nx = a.nx;
-    pv.ny = a.ny;
-    pv.x0 = a.x0;
-    pv.y0 = a.y0;
-    pv.dx = a.dx;
-    pv.dy = a.dy;
-    pv.t = a.dt_from_dev ? a.ds->t : a.t;
-    pv.dt = a.dt_from_dev ? a.ds->dt : a.dt;
-    pv.n_strips = a.n_strips;
-    pv.n_segs = a.n_segs;
-    pv.seg_len = a.seg_len;
-    pv.total_warps = a.n_strips * a.n_segs;
-    pv.partials = a.partials;
-    pv.ds = a.ds;
-    pv.cur = nullptr;
-    pv.done = nullptr;
-    pv.copy_if_idle = 1;
+    const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};
     step2d_body<T, K, B, PHYS, COMP, MLPI>(a, pv, gw);
 }
 
@@ -659,25 +770,24 @@ __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, con
     ProbView<T> pv;
     T* A = const_cast<T*>(bufA) + pb.offset;
     T* Bb = bufB + pb.offset;
-    pv.uin = cur ? Bb : A;
-    pv.uout = cur ? A : Bb;
-    pv.nx = pb.nx;
-    pv.ny = pb.ny;
-    pv.x0 = pb.x0;
-    pv.y0 = pb.y0;
-    pv.dx = pb.dx;
-    pv.dy = pb.dy;
-    pv.t = ds->t;
-    pv.dt = ds->dt;
-    pv.n_strips = pb.n_strips;
-    pv.n_segs = pb.n_segs;
-    pv.seg_len = a.seg_len;
-    pv.total_warps = pb.n_strips * pb.n_segs;
-    pv.partials = a.partials + (size_t)pb.warp0 * Step2D<T, K, B, PHYS>::NRED;
-    pv.ds = ds;
-    pv.cur = curs + tk.x;
-    pv.done = done;
-    pv.copy_if_idle = 0;
+    pv.uin_ = cur ? Bb : A;
+    pv.uout_ = cur ? A : Bb;
+    pv.nx_ = pb.nx;
+    pv.ny_ = pb.ny;
+    pv.x0_ = pb.x0;
+    pv.y0_ = pb.y0;
+    pv.dx_ = pb.dx;
+    pv.dy_ = pb.dy;
+    pv.t_ = ds->t;
+    pv.dt_ = ds->dt;
+    pv.n_strips_ = pb.n_strips;
+    pv.n_segs_ = pb.n_segs;
+    pv.seg_len_ = a.seg_len;
+    pv.total_warps_ = pb.n_strips * pb.n_segs;
+    pv.partials_ = a.partials + (size_t)pb.warp0 * Step2D<T, K, B, PHYS>::NRED;
+    pv.ds_ = ds;
+    pv.cur_ = curs + tk.x;
+    pv.done_ = done;
     step2d_body<T, K, B, PHYS>(a, pv, tk.y);
 }
 
