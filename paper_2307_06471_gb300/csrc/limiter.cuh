@@ -192,6 +192,29 @@ __device__ __forceinline__ bool positivity_cell(T (&u)[NV][NM], T gamma, T eps) 
             const int f = (q - NQV) / NQ, p = (q - NQV) % NQ;
             return T(f == 0 ? tb.tE[p][m] : f == 1 ? tb.tW[p][m] : f == 2 ? tb.tN[p][m] : tb.tS[p][m]);
         };
+        // Shortcut: |phi_m| <= 1 on the reference cell, so rho >= rho_lo =
+        // rhobar - sum |rho_m| and p >= (gamma-1)(E_lo - (Mx^2 + My^2)/(2 rho_lo))
+        // at every point.  When both bounds clear eps by a margin far above
+        // the rounding of the point values, the scaling below would change
+        // nothing: return at once.
+        {
+            T sr = T(0), se = T(0), sx = T(0), sy = T(0);
+#pragma unroll
+            for (int m = 1; m < NM; ++m) {
+                sr += fabs(u[0][m]);
+                sx += fabs(u[1][m]);
+                sy += fabs(u[2][m]);
+                se += fabs(u[3][m]);
+            }
+            const T rlo = u[0][0] - sr;
+            const T elo = u[3][0] - se;
+            const T mx = fabs(u[1][0]) + sx, my = fabs(u[2][0]) + sy;
+            const T margin = T(1e-4);
+            if (rlo > eps + margin * (fabs(u[0][0]) + sr)) {
+                const T plo = (gamma - T(1)) * (elo - (mx * mx + my * my) / (T(2) * rlo));
+                if (plo > eps + margin * (gamma - T(1)) * (fabs(u[3][0]) + se)) return false;
+            }
+        }
         bool changed = false;
         // step 1: density
         const T rbar = u[0][0];
