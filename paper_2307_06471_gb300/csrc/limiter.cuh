@@ -79,6 +79,60 @@ __device__ __forceinline__ void euler_eig(const T* u, T gamma, T R[4][4], T L[4]
     (void)wv;
 }
 
+// Left eigenvectors only (the troubled-cell test needs L; R only when a cell
+// is limited).
+template <class T, int AXIS>
+__device__ __forceinline__ void euler_left(const T* u, T gamma, T L[4][4]) {
+    const T gm1 = gamma - T(1);
+    const T ir = T(1) / u[0];
+    const T w = u[1] * ir, v = u[2] * ir;
+    const T q2 = w * w + v * v;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    const T c2 = gamma * p * ir;
+    const T c = sqrt(c2 > T(0) ? c2 : T(0));
+    const T vn = AXIS == 0 ? w : v;
+    const T vt = AXIS == 0 ? v : w;
+    const int in = 1 + AXIS, it = 2 - AXIS;
+    const T ic = T(1) / c;
+    const T b1 = gm1 * ic * ic;
+    const T b2 = T(0.5) * b1 * q2;
+    L[0][0] = T(0.5) * (b2 + vn * ic);
+    L[0][in] = -T(0.5) * (b1 * vn + ic);
+    L[0][it] = -T(0.5) * b1 * vt;
+    L[0][3] = T(0.5) * b1;
+    L[1][0] = T(1) - b2;
+    L[1][in] = b1 * vn;
+    L[1][it] = b1 * vt;
+    L[1][3] = -b1;
+    L[2][0] = -vt;
+    L[2][in] = T(0);
+    L[2][it] = T(1);
+    L[2][3] = T(0);
+    L[3][0] = T(0.5) * (b2 - vn * ic);
+    L[3][in] = -T(0.5) * (b1 * vn - ic);
+    L[3][it] = -T(0.5) * b1 * vt;
+    L[3][3] = T(0.5) * b1;
+}
+
+template <class T, int AXIS>
+__device__ __forceinline__ void euler_right(const T* u, T gamma, T R[4][4]) {
+    const T gm1 = gamma - T(1);
+    const T ir = T(1) / u[0];
+    const T w = u[1] * ir, v = u[2] * ir;
+    const T q2 = w * w + v * v;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    const T c2 = gamma * p * ir;
+    const T c = sqrt(c2 > T(0) ? c2 : T(0));
+    const T H = (u[3] + p) * ir;
+    const T vn = AXIS == 0 ? w : v;
+    const T vt = AXIS == 0 ? v : w;
+    const int in = 1 + AXIS, it = 2 - AXIS;
+    R[0][0] = T(1); R[0][1] = T(1); R[0][2] = T(0); R[0][3] = T(1);
+    R[in][0] = vn - c; R[in][1] = vn; R[in][2] = T(0); R[in][3] = vn + c;
+    R[it][0] = vt; R[it][1] = vt; R[it][2] = T(1); R[it][3] = vt;
+    R[3][0] = H - vn * c; R[3][1] = T(0.5) * q2; R[3][2] = vt; R[3][3] = H + vn * c;
+}
+
 // Limit one cell in place.  u[v][m] modal coefficients, nb* neighbour
 // averages.  Returns true if the cell was troubled.
 // mode -1: the TVB test decides; 0: leave the cell; 1: limit it (slopes
@@ -94,10 +148,9 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
     T mx[NV], my[NV];
     bool flag = false;
     if (NV == 4) {
-        T R[4][4], L[4][4];
-        // x direction
-        euler_eig<T, 0>(avg, gamma, R, L);
-        T c1[4], c2[4], c3[4];
+        T L[4][4], mxc[4], myc[4];
+        // x direction: characteristic values and the modified minmod
+        euler_left<T, 0>(avg, gamma, L);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             T s1 = 0, s2 = 0, s3 = 0;
@@ -107,23 +160,11 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
                 s2 += L[f][v] * (nbE[v] - avg[v]);
                 s3 += L[f][v] * (avg[v] - nbW[v]);
             }
-            c1[f] = s1; c2[f] = s2; c3[f] = s3;
-        }
-        T m[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            m[f] = tvb_minmod(c1[f], c2[f], c3[f], Mdx2);
-            flag |= (m[f] != c1[f]);
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            T s = 0;
-#pragma unroll
-            for (int f = 0; f < 4; ++f) s += R[v][f] * m[f];
-            mx[v] = s;
+            mxc[f] = tvb_minmod(s1, s2, s3, Mdx2);
+            flag |= (mxc[f] != s1);
         }
         // y direction
-        euler_eig<T, 1>(avg, gamma, R, L);
+        euler_left<T, 1>(avg, gamma, L);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             T s1 = 0, s2 = 0, s3 = 0;
@@ -133,19 +174,29 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
                 s2 += L[f][v] * (nbN[v] - avg[v]);
                 s3 += L[f][v] * (avg[v] - nbS[v]);
             }
-            c1[f] = s1; c2[f] = s2; c3[f] = s3;
+            myc[f] = tvb_minmod(s1, s2, s3, Mdy2);
+            flag |= (myc[f] != s1);
         }
+        if (mode >= 0) flag = mode == 1;
+        if (flag) {
+            // back to conserved variables only for limited cells
+            T R[4][4];
+            euler_right<T, 0>(avg, gamma, R);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            m[f] = tvb_minmod(c1[f], c2[f], c3[f], Mdy2);
-            flag |= (m[f] != c1[f]);
-        }
+            for (int v = 0; v < 4; ++v) {
+                T s = 0;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            T s = 0;
+                for (int f = 0; f < 4; ++f) s += R[v][f] * mxc[f];
+                mx[v] = s;
+            }
+            euler_right<T, 1>(avg, gamma, R);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) s += R[v][f] * m[f];
-            my[v] = s;
+            for (int v = 0; v < 4; ++v) {
+                T s = 0;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) s += R[v][f] * myc[f];
+                my[v] = s;
+            }
         }
     } else {
 #pragma unroll

@@ -25,6 +25,14 @@
 #include "limiter.cuh"
 #include "mlp_warp.cuh"
 
+// launch bounds of the single-problem step kernel (tuning knobs)
+#ifndef CRK_STEP_MAXT
+#define CRK_STEP_MAXT 256
+#endif
+#ifndef CRK_STEP_MINB2
+#define CRK_STEP_MINB2 1
+#endif
+
 namespace crk {
 
 // a0 += x0 * c, a1 += x1 * c: one packed FP32x2 FMA on sm_100+ for float
@@ -730,7 +738,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
 template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false>
-__global__ void __launch_bounds__(256) step2d_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(CRK_STEP_MAXT, CRK_STEP_MINB2) step2d_kernel(const StepArgs a) {
     if constexpr (MLPI) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
         MlpSmem& mw = *reinterpret_cast<MlpSmem*>(smem_raw + mlp_smem_offset<T, K, B, PHYS>(a.s, blockDim.x));
