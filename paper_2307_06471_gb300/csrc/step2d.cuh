@@ -25,6 +25,11 @@
 #include "limiter.cuh"
 #include "mlp_warp.cuh"
 
+// where the per-row accumulator sum_i b_i vol_i lives: 0 registers, 1 the
+// thread's shared-memory slot (tuning knob)
+#ifndef CRK_V_SMEM
+#define CRK_V_SMEM 0
+#endif
 // launch bounds of the single-problem step kernel (tuning knobs)
 #ifndef CRK_STEP_MAXT
 #define CRK_STEP_MAXT 256
@@ -59,9 +64,11 @@ struct Step2D {
     static constexpr int NDOF = NV * NM;
     static constexpr int NRED = NV + 2;   // reduction slots: maxspeed, sums[NV], troubled
 
-    // T elements of private shared memory per thread for s stages
+    // T elements of private shared memory per thread for s stages: L_j
+    // (j < s-1), north traces per stage, pending update, and (CRK_V_SMEM) the
+    // row's sum_i b_i vol_i
     static __host__ __device__ constexpr int smem_per_thread(int s) {
-        return (s - 1) * NDOF + s * NQ * NV + NDOF;
+        return (s - 1) * NDOF + s * NQ * NV + NDOF + (CRK_V_SMEM ? NDOF : 0);
     }
 };
 
@@ -158,6 +165,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const int S = a.s;
     const int offN = (S - 1) * C::NDOF;
     const int offP = offN + S * NQ * NV;
+    const int offV = offP + C::NDOF;
     auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
 
     const int lane = tid & 31;
@@ -312,13 +320,17 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         }
 
         // ---- stages ---------------------------------------------------------------
-        T V[NV][NM];      // sum_i b_i * volume term
+        T Vr[CRK_V_SMEM ? 1 : NV][CRK_V_SMEM ? 1 : NM];   // sum_i b_i * volume term (registers)
+        auto V = [&](int v, int m) -> T& {
+            if constexpr (CRK_V_SMEM) return slot(offV + v * NM + m);
+            else return Vr[v][m];
+        };
         T FE[NQ][NV];     // sum_i b_i fhat on the east face
         T FS[NQ][NV];     // sum_i b_i fhat on the south face
 #pragma unroll
         for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int m = 0; m < NM; ++m) V[v][m] = T(0);
+            for (int m = 0; m < NM; ++m) V(v, m) = T(0);
 #pragma unroll
         for (int p = 0; p < NQ; ++p)
 #pragma unroll
@@ -411,12 +423,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                     for (int v = 0; v < NV; v += 2)
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) pfma(V[v][m], V[v + 1][m], vol[v][m], vol[v + 1][m], bi);
+                        for (int m = 0; m < NM; ++m) pfma(V(v, m), V(v + 1, m), vol[v][m], vol[v + 1][m], bi);
                 } else {
 #pragma unroll
                     for (int v = 0; v < NV; ++v)
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) V[v][m] += bi * vol[v][m];
+                        for (int m = 0; m < NM; ++m) V(v, m) += bi * vol[v][m];
                 }
             }
             // face traces
@@ -628,7 +640,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
                     sy -= FS[p][v] * T(tb.pS[p][m]);
                 }
-                P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V[v][m]);
+                P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V(v, m));
             }
         if (r == ny - 1 && !pery) {
             // top boundary: north face flux from the stored north traces
