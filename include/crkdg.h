@@ -177,6 +177,17 @@ int crkdg_positivity(crkdg_ctx* ctx, double eps);
  * last crkdg_advance.  No host synchronisation (2D only). */
 int crkdg_step_device(crkdg_ctx* ctx);
 
+/* One step of the original RKDG method for comparison (eq. (2.6) in the
+ * Shu--Osher SSP form of Sec. 3.2.1: order 2 or 3), with every stage using
+ * div^DG f and the final-stage limiters (crkdg_limit / crkdg_positivity)
+ * applied after every stage, as the paper does for RKDG (Sec. 4.2).  Runs as
+ * order forward-Euler DG passes (each needs neighbour data), limiter passes
+ * and linear combinations; needs a third state copy (allocated on first use).
+ * Boundary data of the stages at t, t + dt (and t + dt/2 for order 3).
+ * 2D FP32/FP64.  The device dt of crkdg_step_device is not updated: use
+ * crkdg_cfl_dt. */
+int crkdg_rkdg_step(crkdg_ctx* ctx, double dt, int order);
+
 /* Fixed-dt run of n_steps steps.  1D meshes of up to 960 cells run the whole
  * sequence in one single-block launch (block barrier between steps). */
 int crkdg_run_fixed(crkdg_ctx* ctx, int n_steps, double dt);

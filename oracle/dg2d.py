@@ -238,3 +238,18 @@ def run(dg, u, t0, T, step, dt=None, cfl=None, max_steps=None):
         t += d
         n += 1
     return u, n, t
+
+
+def rkdg_ssp_step(dg, u, t, dt, order, limiter=None):
+    """RKDG in the Shu--Osher SSP-RK2 / SSP-RK3 forms (convex combinations of
+    forward Euler steps, Sec. 3.2.1) with the limiter after every stage
+    (Sec. 4.2); boundary data of the stages at t, t + dt (, t + dt/2)."""
+    lim = limiter if limiter is not None else (lambda v, tt: v)
+    if order == 2:
+        u1 = lim(u - dt * dg.L_dg(u, t), t + dt)
+        return lim(0.5 * u + 0.5 * (u1 - dt * dg.L_dg(u1, t + dt)), t + dt)
+    if order == 3:
+        u1 = lim(u - dt * dg.L_dg(u, t), t + dt)
+        u2 = lim(0.75 * u + 0.25 * (u1 - dt * dg.L_dg(u1, t + dt)), t + 0.5 * dt)
+        return lim(u / 3.0 + 2.0 / 3.0 * (u2 - dt * dg.L_dg(u2, t + 0.5 * dt)), t + dt)
+    raise ValueError(order)

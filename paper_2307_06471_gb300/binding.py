@@ -60,6 +60,7 @@ _SIGS = {
     "crkdg_advance": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "crkdg_run_fixed": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "crkdg_step_device": (C.c_int, [C.c_void_p]),
+    "crkdg_rkdg_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "crkdg_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_positivity": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_conservation": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -234,6 +235,9 @@ class Solver:
 
     def advance(self, n_steps, cfl, t_end, capture=False):
         _check(lib().crkdg_advance(self.ctx, int(n_steps), float(cfl), float(t_end), 1 if capture else 0))
+
+    def rkdg_step(self, dt, order=3):
+        _check(lib().crkdg_rkdg_step(self.ctx, float(dt), int(order)))
 
     def step_device(self):
         _check(lib().crkdg_step_device(self.ctx))

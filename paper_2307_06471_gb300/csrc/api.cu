@@ -73,6 +73,8 @@ struct crkdg_ctx {
     double pp_pending;    // positivity floor of the pending limit
     int seg_rows, wpb;
     int kphys;   // kernel physics id
+    void* u3 = nullptr;           // third state copy (RKDG baseline), allocated on first use
+    double* d_tab_fe = nullptr;   // forward-Euler tableau (RKDG stages)
     const float* mlp = nullptr;   // learned indicator parameters (device), owned by a crkdg_mlp
     float mlp_zlo = 0.f, mlp_zhi = 0.f;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -334,6 +336,8 @@ void crkdg_destroy(crkdg_ctx* c) {
     if (c->d_state) cudaFree(c->d_state);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_flags) cudaFree(c->d_flags);
+    if (c->u3) cudaFree(c->u3);
+    if (c->d_tab_fe) cudaFree(c->d_tab_fe);
     delete c;
 }
 
@@ -531,6 +535,89 @@ int crkdg_step_device(crkdg_ctx* c) {
     if (r) return r;
     c->t_known = false;
     c->pending = c->limiter_on || c->pp_eps > 0.0;
+    c->M_pending = c->M;
+    c->pp_pending = c->pp_eps;
+    return CRKDG_OK;
+}
+
+// one forward-Euler DG step out = in - dt div^DG f(in) at time t (the
+// fused step kernel with a one-stage tableau), no limiting on load
+static int enqueue_fe(crkdg_ctx* c, const void* in, void* out, double t, double dt) {
+    StepArgs a = base_args(c);
+    a.uin = in;
+    a.uout = out;
+    a.t = t;
+    a.dt = dt;
+    a.s = 1;
+    a.tab = c->d_tab_fe;
+    int ns, nseg;
+    strips_segs(c, c->seg_rows, &ns, &nseg);
+    a.seg_len = c->seg_rows;
+    a.n_strips = ns;
+    a.n_segs = nseg;
+    int r = ensure_partials(c, (size_t)ns * nseg * 8);
+    if (r) return r;
+    a.partials = c->d_partials;
+    CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+    return CRKDG_OK;
+}
+
+static int enqueue_limit_buf(crkdg_ctx* c, void* u, double t, double M, double pp) {
+    if (M < 0.0 && !(pp > 0.0)) return CRKDG_OK;
+    StepArgs a = base_args(c);
+    a.M = M;
+    a.pp_eps = pp;
+    a.t = t;
+    CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, u, c->d_flags, c->stream));
+    return CRKDG_OK;
+}
+
+int crkdg_rkdg_step(crkdg_ctx* c, double dt, int order) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2 || c->precision == CRKDG_F32C) return fail(CRKDG_EUNSUPPORTED, "RKDG is built for 2D FP32/FP64");
+    if (order != 2 && order != 3) return fail(CRKDG_EINVAL, "order must be 2 or 3 (Shu--Osher SSP forms)");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(CRKDG_EINVAL, "dt must be positive and finite");
+    if (!c->u3) {
+        if (cudaMalloc(&c->u3, c->elems * c->esize) != cudaSuccess) return fail(CRKDG_ENOMEM, "cudaMalloc failed");
+        double fe[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
+        fe[crk::MAXS * crk::MAXS] = 1.0;   // b_1 = 1, c_1 = 0
+        if (cudaMalloc(&c->d_tab_fe, sizeof(fe)) != cudaSuccess) return fail(CRKDG_ENOMEM, "cudaMalloc failed");
+        CK(cudaMemcpy(c->d_tab_fe, fe, sizeof(fe), cudaMemcpyHostToDevice));
+    }
+    if (!c->t_known) {
+        CK(cudaMemcpyAsync(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->t_known = true;
+    }
+    const double t = c->t;
+    void* U = c->u[c->cur];
+    void* A = c->u[c->cur ^ 1];
+    void* B = c->u3;
+    const double M = c->limiter_on ? c->M : -1.0, pp = c->pp_eps;
+    int r = CRKDG_OK;
+    // u^n as stored is pending the limiter of the previous step
+    if (c->pending) r = enqueue_limit_buf(c, U, t, c->M_pending, c->pp_pending);
+    // u1 = Lim(u^n + dt L(u^n)), boundary data at t
+    if (!r) r = enqueue_fe(c, U, A, t, dt);
+    if (!r) r = enqueue_limit_buf(c, A, t + dt, M, pp);
+    if (order == 2) {
+        // u^{n+1} = Lim(1/2 u^n + 1/2 (u1 + dt L(u1))), data at t + dt
+        if (!r) r = enqueue_fe(c, A, B, t + dt, dt);
+        if (!r) CK(crk::launch_axpby(c->precision, A, U, B, 0.5, 0.5, c->elems, c->stream));
+    } else {
+        // u2 = Lim(3/4 u^n + 1/4 (u1 + dt L(u1))), data at t + dt
+        if (!r) r = enqueue_fe(c, A, B, t + dt, dt);
+        if (!r) CK(crk::launch_axpby(c->precision, A, U, B, 0.75, 0.25, c->elems, c->stream));
+        if (!r) r = enqueue_limit_buf(c, A, t + 0.5 * dt, M, pp);
+        // u^{n+1} = Lim(1/3 u^n + 2/3 (u2 + dt L(u2))), data at t + dt/2
+        if (!r) r = enqueue_fe(c, A, B, t + 0.5 * dt, dt);
+        if (!r) CK(crk::launch_axpby(c->precision, A, U, B, 1.0 / 3.0, 2.0 / 3.0, c->elems, c->stream));
+    }
+    if (r) return r;
+    CK(crk::launch_set_time(c->d_state, t + dt, c->stream));
+    c->cur ^= 1;
+    c->t = t + dt;
+    c->pending = (c->limiter_on || c->pp_eps > 0.0);
     c->M_pending = c->M;
     c->pp_pending = c->pp_eps;
     return CRKDG_OK;

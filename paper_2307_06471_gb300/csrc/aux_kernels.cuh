@@ -190,4 +190,12 @@ __global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned lon
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
 }
 
+// out = alpha * x + beta * y over n elements (RKDG Shu--Osher combinations)
+template <class T>
+__global__ void axpby_kernel(T* __restrict__ out, const T* __restrict__ x, const T* __restrict__ y, double alpha,
+                             double beta, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = T(alpha) * x[i] + T(beta) * y[i];
+}
+
 }  // namespace crk

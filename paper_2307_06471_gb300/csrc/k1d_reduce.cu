@@ -122,6 +122,27 @@ cudaError_t launch_project(int dim, int phys, int prec, int k, int basis, const 
     return prec == 0 ? project2d_adv_f32(k, basis, vals, u, ncell, st) : project2d_adv_f64(k, basis, vals, u, ncell, st);
 }
 
+cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,
+                         cudaStream_t st) {
+    const int blocks = 4 * 152;
+    if (prec == 1)
+        axpby_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double*>(out), static_cast<const double*>(x),
+                                                     static_cast<const double*>(y), alpha, beta, n);
+    else
+        axpby_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float*>(out), static_cast<const float*>(x),
+                                                    static_cast<const float*>(y), alpha, beta, n);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void set_time_kernel(DevState* ds, double t) { ds->t = t; }
+}  // namespace
+
+cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st) {
+    set_time_kernel<<<1, 1, 0, st>>>(ds, t);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step2d(int phys, int prec, int k, int basis, const StepArgs& a, int wpb, cudaStream_t st) {
     if (prec == 2) return step2d_euler_f32c(k, basis, a, wpb, st);
     if (phys == PHYS_EULER)

@@ -48,6 +48,11 @@ cudaError_t reduce_euler_f32c(const void* u, int nx, int ny, int nm, double dx, 
 // FP32 2D Euler k = 2 step with the fused learned indicator
 cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
 
+// out = alpha x + beta y (n elements of the state precision), and DevState.t = t
+cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,
+                         cudaStream_t st);
+cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st);
+
 struct BatchProblem;
 #define CRK_DECL_B(NAME)                                                                                     \
     cudaError_t batch2d_##NAME(int k, int basis, const StepArgs& a, const BatchProblem* probs, const int2* tasks, \

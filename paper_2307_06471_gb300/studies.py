@@ -6,6 +6,9 @@ paper_2307_06471_gb300.studies <name>): each prints one JSON line.
             FP64): DOF-updates/s of the batched, graph-replayed steps
   vortex    isentropic vortex, Q^2, RK4, CFL 0.1, periodic [0,10]^2, to T:
             density L1 error, order over the sizes, FP64 total drift, time
+  compact   cRKDG against the original RKDG (Shu--Osher SSP-RK3, limiter
+            every stage) on the 1920 x 480 double Mach reflection: device
+            time per step and per unit simulated time at the paper's CFL
   learned   learned troubled-cell indicator: labels from ensemble runs,
             training with the library's kernels, evaluation on the
             shock-vortex problem (miss / false-flag rates against TVB, L1 vs an
@@ -262,9 +265,54 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
     return out
 
 
+def compact(nx=1920, ny=480, steps=100, precision="f32"):
+    """cRKDG (one fused launch per step) against the original RKDG (SSP-RK3
+    in Shu--Osher form, limiter after every stage) on the double Mach
+    reflection, each at the paper's CFL for P^2 (0.16 and 0.18, Sec. 4.2)."""
+    import torch
+    import crkdg_inputs as inp
+    import bench
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+    P = B.F32 if precision == "f32" else B.F64
+    stream = torch.cuda.Stream()
+    st = inp.dmr_states()
+    out = {"study": "compact", "mesh": "%dx%d" % (nx, ny), "precision": precision, "steps": steps}
+    for name, cfl in (("crkdg", 0.16), ("rkdg", 0.18)):
+        mesh, _ = bench.dmr_mesh(B, inp, nx, ny)
+        s = B.Solver(mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, P, stream=stream.cuda_stream)
+        s.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+        s.limit(50.0)
+        s.positivity(1e-10)
+        for _ in range(5):
+            dt = s.cfl_dt(cfl)
+            s.step(dt) if name == "crkdg" else s.rkdg_step(dt, 3)
+        torch.cuda.synchronize()
+        t0 = s.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(steps):
+            dt = s.cfl_dt(cfl)                       # host dt for both (same overhead)
+            e0.record(stream)
+            s.step(dt) if name == "crkdg" else s.rkdg_step(dt, 3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        sim = s.time() - t0
+        out[name] = {"cfl": cfl, "ms_per_step": ms / steps, "sim_time": sim,
+                     "device_ms_per_unit_time": ms / sim, "status": s.sync()[1],
+                     "launches_per_step": 1 if name == "crkdg" else 9,
+                     "neighbour_passes_per_step": 1 if name == "crkdg" else 3}
+        s.close()
+    out["rkdg_over_crkdg_time_to_solution"] = out["rkdg"]["device_ms_per_unit_time"] / out["crkdg"]["device_ms_per_unit_time"]
+    return out
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["vortex", "ensemble", "learned"])
+    ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -275,6 +323,8 @@ if __name__ == "__main__":
         r = vortex(tuple(int(x) for x in a.sizes.split(",")), a.T, a.precision)
     elif a.study == "learned":
         r = learned()
+    elif a.study == "compact":
+        r = compact(precision=a.precision)
     else:
         r = ensemble(a.n, a.steps, a.precision)
     print(json.dumps(r, default=float))

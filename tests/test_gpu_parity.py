@@ -347,3 +347,43 @@ def test_checkpoint_resume_is_bitwise(tmp_path):
     b.advance(5, 0.16, 0.2)
     assert np.array_equal(b.get_state(), want)
     assert b.time() == t_want
+
+
+# -- original RKDG for comparison (Shu--Osher SSP forms, limiter every stage) -------------------
+@pytest.mark.parametrize("order", [2, 3])
+def test_rkdg_matches_oracle_on_dmr(order):
+    from oracle.dg2d import rkdg_ssp_step
+    from oracle.limiter import positivity_limit
+    bcs, st = _dmr_bcs()
+    nx, ny = 64, 17
+    gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, "f64")
+    u = dg.project(lambda X, Y: inp.dmr_ic(X, Y, st))
+    gs.set_state(to_planes(u), 0.0)
+    gs.limit(50.0)
+    gs.positivity(1e-10)
+    lim = lambda v, tt: positivity_limit(dg, tvb_limit(dg, v, 50.0, tt)[0], 1e-10)
+    w = lim(u, 0.0)
+    t = 0.0
+    for _ in range(3):
+        dt = gs.cfl_dt(0.18)
+        gs.rkdg_step(dt, order)
+        w = rkdg_ssp_step(dg, w, t, dt, order, limiter=lim)
+        t += dt
+    assert rel_err(from_planes(gs.get_state()), w) < 1e-12
+
+
+def test_rkdg_stencil_is_a_diamond_on_gpu():
+    nx, ny = 40, 36
+    gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f64")
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=9)
+    v = u.copy()
+    c = (17, 20)
+    v[c] += 1e-3 * np.abs(u[c])
+    res = []
+    for s_ in (u, v):
+        gs.set_state(to_planes(s_), 0.0)
+        gs.rkdg_step(1e-3, 3)
+        res.append(gs.get_state())
+    ch = {tuple(p) for p in np.argwhere(np.any(res[0] != res[1], axis=(0, 1)))}
+    y, x = c
+    assert ch == {(y + i, x + j) for i in range(-3, 4) for j in range(-3, 4) if abs(i) + abs(j) <= 3}

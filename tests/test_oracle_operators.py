@@ -199,3 +199,14 @@ def test_upwind_p0_advection_is_first_order_upwind():
     lam = 2.0 * dt * N
     want = u[:, 0, 0] - lam * (u[:, 0, 0] - np.roll(u[:, 0, 0], 1))
     assert np.max(np.abs(got - want)) < 1e-14
+
+
+def test_rkdg_ssp_2d_matches_butcher_form_for_linear_problems():
+    """For linear advection SSP-RK3 in Shu--Osher form and in Butcher form
+    are the same method: one step agrees to roundoff."""
+    from oracle.dg2d import rkdg_ssp_step
+    dg = DG2D(7, 6, (0, 1.4, 0, 1.2), 2, "P", Advection([1.0, 0.5]), PER)
+    u = inp.random_modal_state(6, 7, 2, "P", "advection", seed=31)
+    a = rkdg_ssp_step(dg, u, 0.0, 0.01, 3)
+    b = rkdg2(dg, u, 0.0, 0.01, TB.SSPRK3)
+    assert np.max(np.abs(a - b)) < 1e-14
