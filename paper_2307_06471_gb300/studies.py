@@ -310,9 +310,85 @@ def compact(nx=1920, ny=480, steps=100, precision="f32"):
     return out
 
 
+def advection1d(N=160, steps=1600):
+    """u_t + u_x = 0 on periodic [0, 2 pi], u0 = sin x, P^2, SSP-RK3,
+    dt = 0.1 h (CFL 0.1), T = 2 pi: the whole run in one single-block launch.
+    L1 / Linf error of u against sin(x - T) = sin x, and the mass drift."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+    mesh = B.make_mesh(1, N, 1, (0.0, 2 * math.pi, 0.0, 1.0), [B.BC_PERIODIC] * 4)
+    s = B.Solver(mesh, 2, B.BASIS_P, GTB.SSPRK3, B.ADVECTION, B.F64, beta=(1.0, 0.0))
+    s.project_function(lambda X: np.sin(X)[..., None])
+    m0 = s.conservation()
+    dt = 2 * math.pi / steps
+    s.run_fixed(1, dt)                      # warm-up (module load)
+    s.project_function(lambda X: np.sin(X)[..., None])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.run_fixed(steps, dt)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    u = s.get_state()[0, :, 0, :]            # [m][x]
+    g, w = L.leggauss(5)
+    h = 2 * math.pi / N
+    xc = (np.arange(N) + 0.5) * h
+    X = xc[None, :] + 0.5 * h * g[:, None]
+    uh = sum(u[m][None, :] * L.legval(g, np.eye(3)[m])[:, None] for m in range(3))
+    e = np.abs(uh - np.sin(X - 2 * math.pi))
+    m1 = s.conservation()
+    out = {"study": "advection1d", "N": N, "steps": steps, "wall_s": wall, "us_per_step": 1e6 * wall / steps,
+           "L1_mean": float(np.sum(e * w[:, None]) * 0.5 * h / (2 * math.pi)), "Linf": float(e.max()),
+           "mass_drift_abs": float(abs(m1[0] - m0[0])), "launches": 1}
+    s.close()
+    return out
+
+
+def advection2d_inflow(sizes=(10, 20, 40, 80), T=0.4, k=3, basis="Q"):
+    """Cartesian analogue of the paper's 2D boundary-error example: u_t + u_x
+    + u_y = 0 on [-1,1]^2, u0 = sin(pi x) sin(pi y), exact data
+    sin(pi (x - t)) sin(pi (y - t)) imposed on the inflow sides (W, S) at the
+    stage times of the final stage, outflow E, N; P^3/Q^3 with RK4 and
+    dt = h/30 (FP64).  L2 error and order."""
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+    rows = []
+    pp = [1.0, math.pi, 1.0, math.pi, 1.0]
+    for N in sizes:
+        mesh = B.make_mesh(2, N, N, (-1.0, 1.0, -1.0, 1.0), [B.BC_DIRICHLET, B.BC_OUTFLOW, B.BC_DIRICHLET, B.BC_OUTFLOW],
+                           [B.FN_SINE_PROD, 0, B.FN_SINE_PROD, 0], [pp, None, pp, None])
+        s = B.Solver(mesh, k, B.BASIS_Q if basis == "Q" else B.BASIS_P, GTB.RK4, B.ADVECTION, B.F64,
+                     beta=(1.0, 1.0))
+        s.project_function(lambda X, Y: (np.sin(math.pi * X) * np.sin(math.pi * Y))[..., None])
+        h = 2.0 / N
+        n = int(math.ceil(T / (h / 30)))
+        for _ in range(n):
+            s.step(T / n)
+        u = s.get_state()
+        nm = len(_modes(k, basis))
+        g, w = L.leggauss(k + 3)
+        P = lambda i, t: L.legval(t, np.eye(k + 1)[i])
+        phi = np.stack([np.outer(P(i, g), P(j, g)) for (i, j) in _modes(k, basis)])
+        uh = np.einsum("myx,mab->yxab", u[0], phi)
+        xc = -1 + (np.arange(N) + 0.5) * h
+        X = xc[None, :, None, None] + 0.5 * h * g[None, None, :, None]
+        Y = xc[:, None, None, None] + 0.5 * h * g[None, None, None, :]
+        e = uh - np.sin(math.pi * (X - T)) * np.sin(math.pi * (Y - T))
+        l2 = math.sqrt(float(np.sum(e * e * np.outer(w, w)) * 0.25 * h * h))
+        rows.append({"N": N, "L2": l2, "steps": n})
+        s.close()
+    for a, b in zip(rows[:-1], rows[1:]):
+        b["order"] = math.log(a["L2"] / b["L2"]) / math.log(b["N"] / a["N"])
+    return {"study": "advection2d_inflow", "k": k, "basis": basis, "T": T, "rows": rows}
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact"])
+    ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -325,6 +401,10 @@ if __name__ == "__main__":
         r = learned()
     elif a.study == "compact":
         r = compact(precision=a.precision)
+    elif a.study == "advection1d":
+        r = advection1d()
+    elif a.study == "advection2d":
+        r = advection2d_inflow()
     else:
         r = ensemble(a.n, a.steps, a.precision)
     print(json.dumps(r, default=float))
