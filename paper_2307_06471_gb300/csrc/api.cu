@@ -300,12 +300,8 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
             return bail(fail(CRKDG_ENOMEM, "cudaMalloc of the state failed"));
         cudaMemsetAsync(c->u[b], 0, c->elems * c->esize * c->planes, c->stream);
     }
-    double htab[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
-    for (int i = 0; i < crk::MAXS * crk::MAXS; ++i) htab[i] = tab->a[i];
-    for (int i = 0; i < tab->s; ++i) {
-        htab[crk::MAXS * crk::MAXS + i] = tab->b[i];
-        htab[crk::MAXS * crk::MAXS + crk::MAXS + i] = tab->c[i];
-    }
+    unsigned char htab[crk::TAB_BYTES];
+    crk::pack_tableau(tab->s, tab->a, tab->b, tab->c, htab);
     if (cudaMalloc(&c->d_tab, sizeof(htab)) != cudaSuccess ||
         cudaMalloc(&c->d_state, sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&c->d_flags, sizeof(unsigned long long)) != cudaSuccess)
@@ -579,8 +575,9 @@ int crkdg_rkdg_step(crkdg_ctx* c, double dt, int order) {
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(CRKDG_EINVAL, "dt must be positive and finite");
     if (!c->u3) {
         if (cudaMalloc(&c->u3, c->elems * c->esize) != cudaSuccess) return fail(CRKDG_ENOMEM, "cudaMalloc failed");
-        double fe[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
-        fe[crk::MAXS * crk::MAXS] = 1.0;   // b_1 = 1, c_1 = 0
+        const double fa[crk::MAXS * crk::MAXS] = {0}, fb[crk::MAXS] = {1.0}, fc[crk::MAXS] = {0};
+        unsigned char fe[crk::TAB_BYTES];
+        crk::pack_tableau(1, fa, fb, fc, fe);   // forward Euler: s = 1, b_1 = 1, c_1 = 0
         if (cudaMalloc(&c->d_tab_fe, sizeof(fe)) != cudaSuccess) return fail(CRKDG_ENOMEM, "cudaMalloc failed");
         CK(cudaMemcpy(c->d_tab_fe, fe, sizeof(fe), cudaMemcpyHostToDevice));
     }

@@ -240,12 +240,8 @@ int crkdg_batch_create(const crkdg_batch_problem* probs, int n, const int* bc, i
     for (int i = 0; i < 2; ++i)
         if (cudaMalloc(&b->buf[i], b->elems * b->esize) != cudaSuccess)
             return bail(bfail(CRKDG_ENOMEM, "cudaMalloc of the batch state failed"));
-    double htab[crk::MAXS * crk::MAXS + 2 * crk::MAXS] = {0};
-    for (int i = 0; i < crk::MAXS * crk::MAXS; ++i) htab[i] = tab->a[i];
-    for (int i = 0; i < tab->s; ++i) {
-        htab[crk::MAXS * crk::MAXS + i] = tab->b[i];
-        htab[crk::MAXS * crk::MAXS + crk::MAXS + i] = tab->c[i];
-    }
+    unsigned char htab[crk::TAB_BYTES];
+    crk::pack_tableau(tab->s, tab->a, tab->b, tab->c, htab);
     if (cudaMalloc(&b->d_probs, n * sizeof(BatchProblem)) != cudaSuccess ||
         cudaMalloc(&b->d_states, n * sizeof(DevState)) != cudaSuccess ||
         cudaMalloc(&b->d_curs, n * sizeof(int)) != cudaSuccess ||

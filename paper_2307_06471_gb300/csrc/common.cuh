@@ -43,7 +43,7 @@ struct StepArgs {
     DevState* ds;
     double* partials;         // per-warp reduction slots
     int s;
-    const double* tab;        // device: a[MAXS*MAXS] row-major, b[MAXS], c[MAXS]
+    const double* tab;        // device tableau buffer, layout of pack_tableau
     BCSide bc[4];             // W, E, S, N
     int seg_len, n_strips, n_segs;
     int limit;                // 1: limit u^n on load (final-stage limiters of the previous step)
@@ -175,9 +175,39 @@ __device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T*
     }
 }
 
+// Device tableau buffer: FP64 a (MAXS x MAXS, row-major), b, c, followed by
+// FP32 copies of a and b rounded once on the host, so that FP32 kernels take
+// their stage weights without FP64 loads or conversions.
+constexpr int TAB_F64 = MAXS * MAXS + 2 * MAXS;
+constexpr int TAB_F32 = MAXS * MAXS + MAXS;
+constexpr size_t TAB_BYTES = TAB_F64 * sizeof(double) + TAB_F32 * sizeof(float);
+inline void pack_tableau(int s, const double* A, const double* b, const double* c, unsigned char* out) {
+    double d[TAB_F64] = {0};
+    float f[TAB_F32] = {0};
+    for (int i = 0; i < s; ++i) {
+        for (int j = 0; j < s; ++j) d[i * MAXS + j] = A[i * MAXS + j];
+        d[MAXS * MAXS + i] = b[i];
+        d[MAXS * MAXS + MAXS + i] = c[i];
+    }
+    for (int i = 0; i < MAXS * MAXS + MAXS; ++i) f[i] = (float)d[i];
+    for (size_t k = 0; k < sizeof(d); ++k) out[k] = reinterpret_cast<const unsigned char*>(d)[k];
+    for (size_t k = 0; k < sizeof(f); ++k) out[sizeof(d) + k] = reinterpret_cast<const unsigned char*>(f)[k];
+}
+
 __device__ __forceinline__ double tab_a(const StepArgs& a, int i, int j) { return __ldg(a.tab + i * MAXS + j); }
 __device__ __forceinline__ double tab_b(const StepArgs& a, int i) { return __ldg(a.tab + MAXS * MAXS + i); }
 __device__ __forceinline__ double tab_c(const StepArgs& a, int i) { return __ldg(a.tab + MAXS * MAXS + MAXS + i); }
+// the same weights in the kernel's arithmetic type T
+template <class T>
+__device__ __forceinline__ T tab_aT(const StepArgs& a, int i, int j) {
+    if constexpr (sizeof(T) == 4) return __ldg(reinterpret_cast<const float*>(a.tab + TAB_F64) + i * MAXS + j);
+    else return tab_a(a, i, j);
+}
+template <class T>
+__device__ __forceinline__ T tab_bT(const StepArgs& a, int i) {
+    if constexpr (sizeof(T) == 4) return __ldg(reinterpret_cast<const float*>(a.tab + TAB_F64) + MAXS * MAXS + i);
+    else return tab_b(a, i);
+}
 
 template <class T>
 __device__ __forceinline__ T shfl_down(T v, int d) {

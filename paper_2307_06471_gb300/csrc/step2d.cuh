@@ -217,6 +217,18 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const T tdt = T(dt);
     const T Mdx2 = T(a.M * pv.dx() * pv.dx()), Mdy2 = T(a.M * pv.dy() * pv.dy());
     const T gam = T(a.gamma);
+    const bool do_tvb = a.M >= 0.0, do_pp = a.pp_eps > 0.0;
+    const T pp_eps = T(a.pp_eps);
+
+    // FP32 state: the per-cell wave speed and status tests of the epilogue run
+    // in FP32 (GB300's FP64 pipe is 1/64 of its FP32 rate), the column totals
+    // in compensated FP32 (TwoSum), converted to FP64 once per warp
+    constexpr bool F32R = sizeof(T) == 4 && !COMP;
+    T cs_hi[NV], cs_lo[NV];
+    T red_maxT = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cs_hi[v] = cs_lo[v] = T(0);
+    const double adv_speed = PHYS == PHYS_EULER ? 0.0 : fabs(a.beta[0]) / pv.dx() + fabs(a.beta[1]) / pv.dy();
 
     // reduction accumulators (FP64)
     double red_max = 0.0;
@@ -265,6 +277,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         }
     };
     if (a.limit) load_avg(rstart - 1, avg_prev);
+    const double hh_ = pv.dx() > pv.dy() ? pv.dx() : pv.dy();
+    const double mlp_scale = a.M * hh_ * hh_;
 
     for (int r = rstart; r <= rend; ++r) {
         const int ry_ = r < 0 ? r + ny : (r >= ny ? r - ny : r);
@@ -272,7 +286,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         const bool south_bc = (r == 0) && !pery;
         const bool do_south = (r > rstart) || south_bc;   // flux through this row's south face
         const bool keep_north = r < rend || (r == ny - 1 && !pery && out_row);
-        const double yc = pv.y0() + (ry_ + 0.5) * pv.dy();
+        auto yc = [&]() { return pv.y0() + (ry_ + 0.5) * pv.dy(); };
 
         // ---- load u^n (and limit on load) -------------------------------------
         T un[NV][NM];
@@ -306,14 +320,13 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(base + sizeof(MlpSmem)) +
                                        (tid >> 5) * (32 * MLP_INP + 64);
                 float feat[MLP_IN];
-                const double hh = pv.dx() > pv.dy() ? pv.dx() : pv.dy();
-                mlp_features<T, NM>(un, nbE, nbW, avg_next, avg_prev, a.M * hh * hh, feat);
+                mlp_features<T, NM>(un, nbE, nbW, avg_next, avg_prev, mlp_scale, feat);
                 const float z = mlp_warp_logit(mw, feat, stage);
                 mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
             }
-            if (real && a.M >= 0.0)
+            if (real && do_tvb)
                 fl = tvb_limit_cell<T, NV, NM>(un, nbW, nbE, avg_prev, avg_next, Mdx2, Mdy2, gam, mode);
-            if (real && a.pp_eps > 0.0) positivity_cell<T, NV, NM, K, B>(un, gam, T(a.pp_eps));
+            if (real && do_pp) positivity_cell<T, NV, NM, K, B>(un, gam, pp_eps);
             if (out_row && outlane && fl) ++red_trouble;
 #pragma unroll
             for (int v = 0; v < NV; ++v) avg_prev[v] = avg_cur[v];
@@ -337,12 +350,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             for (int v = 0; v < NV; ++v) FE[p][v] = FS[p][v] = T(0);
 
         for (int i = 0; i < S; ++i) {
-            const double bid = tab_b(a, i);
-            const T bi = T(bid);
+            const T bi = tab_bT<T>(a, i);
             const bool need_L = i < S - 1;
-            const bool need_flux = bid != 0.0;
+            const bool need_flux = bi != T(0);
             if (!need_L && !need_flux) continue;
-            const double ti = t0 + tab_c(a, i) * dt;
+            auto ti = [&]() { return t0 + tab_c(a, i) * dt; };   // boundary data only
             // stage state u^(i) = u^n - dt sum_{j<i} a_ij L_j
             T w[NV][NM];
 #pragma unroll
@@ -350,9 +362,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int m = 0; m < NM; ++m) w[v][m] = un[v][m];
             for (int j = 0; j < i; ++j) {
-                const double aijd = tab_a(a, i, j);
-                if (aijd == 0.0) continue;
-                const T aij = T(aijd) * tdt;
+                const T aijT = tab_aT<T>(a, i, j);
+                if (aijT == T(0)) continue;
+                const T aij = aijT * tdt;
                 if constexpr (NV % 2 == 0) {
 #pragma unroll
                     for (int v = 0; v < NV; v += 2)
@@ -518,13 +530,13 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 if (has_bcW && lane == 0) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0(), yc + 0.5 * pv.dy() * tb.xq[p], ti, tE[p]);
+                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0(), yc() + 0.5 * pv.dy() * tb.xq[p], ti(), tE[p]);
                 }
                 if (has_bcE && col == nx - 1) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0() + nx * pv.dx(), yc + 0.5 * pv.dy() * tb.xq[p], ti,
-                                           tWn[p]);
+                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0() + nx * pv.dx(), yc() + 0.5 * pv.dy() * tb.xq[p],
+                                           ti(), tWn[p]);
                 }
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
@@ -541,7 +553,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     T lo[NV];
                     if (south_bc) {
                         const double xp = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
-                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0(), ti, lo);
+                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0(), ti(), lo);
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
@@ -565,6 +577,33 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             // write u^{n+1} of row rw and accumulate the FP64 reductions
             if (!outlane) return;
             const size_t o = (size_t)rw * nx + col;
+            if constexpr (F32R) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {   // TwoSum: cs_hi + cs_lo += P[v][0] exactly
+                    const T x = P[v][0];
+                    const T sum = cs_hi[v] + x;
+                    const T bv = sum - cs_hi[v];
+                    cs_lo[v] += (cs_hi[v] - (sum - bv)) + (x - bv);
+                    cs_hi[v] = sum;
+                }
+                if constexpr (PHYS == PHYS_EULER) {
+                    const T ir = T(1) / P[0][0];
+                    const T w = P[1][0] * ir, vv = P[2][0] * ir;
+                    const T p = ph.gm1 * (P[3][0] - T(0.5) * (P[1][0] * w + P[2][0] * vv));
+                    const T c = sqrt(fmax(gam * p * ir, T(0)));
+                    const T sp = (fabs(w) + c) * rx + (fabs(vv) + c) * ry;
+                    if (!(P[0][0] > T(0)) || !(p > T(0))) status |= ST_NONPHYSICAL;
+                    if (!(sp == sp)) status |= ST_NAN;
+                    red_maxT = fmax(red_maxT, sp);
+                } else {
+                    if (!(P[0][0] == P[0][0])) status |= ST_NAN;
+                }
+                return;
+            }
             double av[NV];
             if constexpr (COMP) {
                 // P holds Delta: u^{n+1} = (hi + lo) + Delta, hi' + lo' by TwoSum
@@ -603,7 +642,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 if (!(av[0] > 0.0) || !(p > 0.0)) status |= ST_NONPHYSICAL;
                 if (!(sp == sp)) status |= ST_NAN;
             } else {
-                sp = fabs(a.beta[0]) / pv.dx() + fabs(a.beta[1]) / pv.dy();
+                sp = adv_speed;
                 if (!(av[0] == av[0])) status |= ST_NAN;
             }
             red_max = fmax(red_max, sp);
@@ -650,9 +689,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int v = 0; v < NV; ++v) FN[p][v] = T(0);
             for (int i = 0; i < S; ++i) {
-                const double bid = tab_b(a, i);
-                if (bid == 0.0) continue;
-                const T bi = T(bid);
+                const T bi = tab_bT<T>(a, i);
+                if (bi == T(0)) continue;
                 const double ti = t0 + tab_c(a, i) * dt;
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
@@ -686,6 +724,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 
     // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
     const double cell = pv.dx() * pv.dy();
+    if constexpr (F32R) {
+        red_max = PHYS == PHYS_EULER ? double(red_maxT) : (outlane && r0 < r1 ? adv_speed : 0.0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red_sum[v] = double(cs_hi[v]) + double(cs_lo[v]);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
