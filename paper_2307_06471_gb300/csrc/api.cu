@@ -107,6 +107,7 @@ StepArgs base_args(const crkdg_ctx* c) {
         a.bc[s].type = c->mesh.bc[s];
         a.bc[s].fn = c->mesh.bc_fn[s];
         for (int j = 0; j < 16; ++j) a.bc[s].p[j] = c->mesh.bc_params[s][j];
+        for (int j = 0; j < 4; ++j) a.bc[s].pf[j] = (float)a.bc[s].p[j];
     }
     a.gamma = c->gamma;
     a.beta[0] = c->beta[0];

@@ -166,8 +166,11 @@ __global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned lon
             int cx = xx[s], cy = yy[s];
             const bool out = (s < 2 && !perx && (cx < 0 || cx >= nx)) || (s >= 2 && !pery && (cy < 0 || cy >= ny));
             if (out) {
-                const double xc = a.x0 + (cx + 0.5) * a.dx, yc = a.y0 + (cy + 0.5) * a.dy;
-                bc_exterior<T, NV>(a.bc[s], s < 2 ? 0 : 1, own, xc, yc, a.t, nb[s]);
+                bc_exterior<T, NV>(a.bc[s], s < 2 ? 0 : 1, own, [&](double& xc, double& yc, double& tc) {
+                    xc = a.x0 + (cx + 0.5) * a.dx;
+                    yc = a.y0 + (cy + 0.5) * a.dy;
+                    tc = a.t;
+                }, nb[s]);
             } else {
                 cx = (cx + nx) % nx;
                 cy = (cy + ny) % ny;

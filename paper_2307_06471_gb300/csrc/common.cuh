@@ -31,6 +31,7 @@ struct BCSide {
     int type;
     int fn;
     double p[16];
+    float pf[4];              // FP32 copy of p[0..3] (the constant exterior state of FN_CONST)
 };
 
 struct StepArgs {
@@ -132,11 +133,19 @@ __device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const 
     for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
 }
 
-// Exterior state at a boundary point (x, y) and time t from the interior
-// state; AXIS is the axis normal to the boundary.
-template <class T, int NV>
-__device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T* uin, double x, double y,
-                                            double t, T* uext) {
+// Value of the sine boundary data (FN_SINE, FN_SINE_PROD); kept out of line
+// so that the double-precision sines are not inlined at every call site.
+static __device__ __noinline__ double bc_sine_value(int prod, double p0, double p1, double p2, double p3, double p4,
+                                             double x, double y, double t) {
+    return prod ? p0 * sin(p1 * (x - p2 * t)) * sin(p3 * (y - p4 * t)) : p0 * sin(p1 * x + p2 * y - p3 * t + p4);
+}
+
+// Exterior state at a boundary point from the interior state; axis is the
+// axis normal to the boundary.  xyt(x, y, t) yields the point and time; it is
+// called only by the boundary functions that depend on them, so outflow,
+// reflecting and constant-state sides cost no FP64 arithmetic.
+template <class T, int NV, class XYT>
+__device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T* uin, const XYT& xyt, T* uext) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) uext[v] = uin[v];
     if (bc.type == BC_OUTFLOW) return;
@@ -145,16 +154,20 @@ __device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T*
         return;
     }
     const double* p = bc.p;
-    switch (bc.fn) {
-        case FN_CONST:
+    if (bc.fn == FN_CONST) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uext[v] = T(p[v]);
-            break;
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (sizeof(T) == 4) uext[v] = bc.pf[v];
+            else uext[v] = T(p[v]);
+        }
+        return;
+    }
+    double x, y, t;
+    xyt(x, y, t);
+    switch (bc.fn) {
         case FN_SINE:
-            uext[0] = T(p[0] * sin(p[1] * x + p[2] * y - p[3] * t + p[4]));
-            break;
         case FN_SINE_PROD:
-            uext[0] = T(p[0] * sin(p[1] * (x - p[2] * t)) * sin(p[3] * (y - p[4] * t)));
+            uext[0] = T(bc_sine_value(bc.fn == FN_SINE_PROD, p[0], p[1], p[2], p[3], p[4], x, y, t));
             break;
         case FN_DMR_BOTTOM:
             if (x < p[4]) {

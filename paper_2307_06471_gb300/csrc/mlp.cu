@@ -211,8 +211,11 @@ __global__ void features_kernel(const StepArgs a, const T* __restrict__ u, float
         int cx = xs[s], cy = ys[s];
         const bool out = (s < 2 && !perx && (cx < 0 || cx >= nx)) || (s >= 2 && !pery && (cy < 0 || cy >= ny));
         if (out) {
-            crk::bc_exterior<T, 4>(a.bc[s], s < 2 ? 0 : 1, own, a.x0 + (cx + 0.5) * a.dx, a.y0 + (cy + 0.5) * a.dy,
-                                   a.t, nb[s]);
+            crk::bc_exterior<T, 4>(a.bc[s], s < 2 ? 0 : 1, own, [&](double& xc, double& yc, double& tc) {
+                xc = a.x0 + (cx + 0.5) * a.dx;
+                yc = a.y0 + (cy + 0.5) * a.dy;
+                tc = a.t;
+            }, nb[s]);
         } else {
             cx = (cx + nx) % nx;
             cy = (cy + ny) % ny;

@@ -135,8 +135,11 @@ __global__ void __launch_bounds__(1024) step1d_kernel(StepArgs a, int n_steps) {
             T tLn[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) tLn[v] = shfl_down(tL[v], 1);
-            if (has_bcW && lane == 0) bc_exterior<T, NV>(a.bc[0], 0, tLn, a.x0, 0.0, ti, tR);
-            if (has_bcE && col == nx - 1) bc_exterior<T, NV>(a.bc[1], 0, tR, a.x0 + nx * a.dx, 0.0, ti, tLn);
+            if (has_bcW && lane == 0)
+                bc_exterior<T, NV>(a.bc[0], 0, tLn, [&](double& x, double& y, double& t) { x = a.x0; y = 0.0; t = ti; }, tR);
+            if (has_bcE && col == nx - 1)
+                bc_exterior<T, NV>(a.bc[1], 0, tR, [&](double& x, double& y, double& t) { x = a.x0 + nx * a.dx; y = 0.0; t = ti; },
+                                   tLn);
             T F[NV];
             llf<T, PHYS, 0>(ph, tR, tLn, F);
 #pragma unroll

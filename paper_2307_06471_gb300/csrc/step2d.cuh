@@ -255,9 +255,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = r < 0 ? 2 : 3;
-            const double xc = pv.x0() + (col + 0.5) * pv.dx();
-            const double yc = r < 0 ? pv.y0() - 0.5 * pv.dy() : pv.y0() + (ny + 0.5) * pv.dy();
-            bc_exterior<T, NV>(a.bc[side], 1, own, xc, yc, t0, out);
+            bc_exterior<T, NV>(a.bc[side], 1, own, [&](double& x, double& y, double& t) {
+                x = pv.x0() + (col + 0.5) * pv.dx();
+                y = r < 0 ? pv.y0() - 0.5 * pv.dy() : pv.y0() + (ny + 0.5) * pv.dy();
+                t = t0;
+            }, out);
         }
     };
     auto load_avg_x = [&](int c, int r, T* out) {
@@ -271,9 +273,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
             const int side = c < 0 ? 0 : 1;
-            const double xc = c < 0 ? pv.x0() - 0.5 * pv.dx() : pv.x0() + (nx + 0.5) * pv.dx();
-            const double yc = pv.y0() + (r + 0.5) * pv.dy();
-            bc_exterior<T, NV>(a.bc[side], 0, own, xc, yc, t0, out);
+            bc_exterior<T, NV>(a.bc[side], 0, own, [&](double& x, double& y, double& t) {
+                x = c < 0 ? pv.x0() - 0.5 * pv.dx() : pv.x0() + (nx + 0.5) * pv.dx();
+                y = pv.y0() + (r + 0.5) * pv.dy();
+                t = t0;
+            }, out);
         }
     };
     if (a.limit) load_avg(rstart - 1, avg_prev);
@@ -286,7 +290,6 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         const bool south_bc = (r == 0) && !pery;
         const bool do_south = (r > rstart) || south_bc;   // flux through this row's south face
         const bool keep_north = r < rend || (r == ny - 1 && !pery && out_row);
-        auto yc = [&]() { return pv.y0() + (ry_ + 0.5) * pv.dy(); };
 
         // ---- load u^n (and limit on load) -------------------------------------
         T un[NV][NM];
@@ -530,13 +533,20 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 if (has_bcW && lane == 0) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], pv.x0(), yc() + 0.5 * pv.dy() * tb.xq[p], ti(), tE[p]);
+                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], [&](double& x, double& y, double& t) {
+                            x = pv.x0();
+                            y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                            t = ti();
+                        }, tE[p]);
                 }
                 if (has_bcE && col == nx - 1) {
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], pv.x0() + nx * pv.dx(), yc() + 0.5 * pv.dy() * tb.xq[p],
-                                           ti(), tWn[p]);
+                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], [&](double& x, double& y, double& t) {
+                            x = pv.x0() + nx * pv.dx();
+                            y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                            t = ti();
+                        }, tWn[p]);
                 }
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
@@ -552,8 +562,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 for (int p = 0; p < NQ; ++p) {
                     T lo[NV];
                     if (south_bc) {
-                        const double xp = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
-                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], xp, pv.y0(), ti(), lo);
+                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], [&](double& x, double& y, double& t) {
+                            x = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                            y = pv.y0();
+                            t = ti();
+                        }, lo);
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
@@ -697,8 +710,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     T lo[NV], hi[NV], F[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
-                    const double xp = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
-                    bc_exterior<T, NV>(a.bc[3], 1, lo, xp, pv.y0() + ny * pv.dy(), ti, hi);
+                    bc_exterior<T, NV>(a.bc[3], 1, lo, [&](double& x, double& y, double& t) {
+                        x = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                        y = pv.y0() + ny * pv.dy();
+                        t = ti;
+                    }, hi);
                     llf<T, PHYS, 1>(ph, lo, hi, F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FN[p][v] += bi * F[v];
