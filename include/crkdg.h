@@ -214,6 +214,27 @@ int crkdg_set_launch(crkdg_ctx* ctx, int seg_rows, int warps_per_block);
 int crkdg_get_launch(const crkdg_ctx* ctx, int* seg_rows, int* warps_per_block);
 int crkdg_autotune(crkdg_ctx* ctx, double* best_us);
 
+/* Where the pending limiter of the previous step's final stage (Remark 2.2)
+ * runs when a 2D step loads u^n: CRKDG_LIMIT_FUSED inside the fused step
+ * (each warp limits the cells it loads), CRKDG_LIMIT_PASS (default) in a
+ * separate in-place pass over all cells, one thread per cell, just before
+ * the step.  Both compute the same limiter (same arithmetic; results agree to
+ * rounding, which can differ where the compiler fuses multiply-adds
+ * differently in the two kernels); the pass costs one extra read of u^n but
+ * spreads the limiter's uneven work (troubled cells gather at shocks) over
+ * the whole GPU instead of the few warps that hold the shock.  The learned
+ * indicator always runs fused.  EINVAL for another mode. */
+enum { CRKDG_LIMIT_FUSED = 0, CRKDG_LIMIT_PASS = 1 };
+int crkdg_set_limit_mode(crkdg_ctx* ctx, int mode);
+int crkdg_get_limit_mode(const crkdg_ctx* ctx, int* mode);
+
+/* Apply the pending limiter (2D) to the stored state now, in place on the
+ * device, as the separate pass above; async on the context stream.  The next
+ * step then loads the state without limiting it again and reports the cells
+ * this pass flagged through crkdg_troubled_count.  No-op when nothing is
+ * pending. */
+int crkdg_apply_limit(crkdg_ctx* ctx);
+
 /* Checkpoint: header + FP64 state; load restores state, t and limiter. */
 int crkdg_save(crkdg_ctx* ctx, const char* path);
 int crkdg_load(crkdg_ctx* ctx, const char* path);

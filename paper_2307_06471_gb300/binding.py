@@ -23,6 +23,7 @@ FN_CONST, FN_SINE, FN_SINE_PROD, FN_DMR_BOTTOM, FN_DMR_TOP = 0, 1, 2, 3, 4
 ADVECTION, EULER = 0, 1
 BASIS_P, BASIS_Q = 0, 1
 F32, F64, F32C = 0, 1, 2
+LIMIT_FUSED, LIMIT_PASS = 0, 1
 FLUX_LLF = 0
 ST_NONPHYSICAL, ST_NAN, ST_TIMEOUT = 1, 2, 4
 
@@ -69,6 +70,9 @@ _SIGS = {
     "crkdg_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "crkdg_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "crkdg_set_limit_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "crkdg_apply_limit": (C.c_int, [C.c_void_p]),
+    "crkdg_get_limit_mode": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "crkdg_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "crkdg_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -273,6 +277,17 @@ class Solver:
 
     def set_launch(self, seg_rows=0, warps_per_block=0):
         _check(lib().crkdg_set_launch(self.ctx, int(seg_rows), int(warps_per_block)))
+
+    def apply_limit(self):
+        _check(lib().crkdg_apply_limit(self.ctx))
+
+    def set_limit_mode(self, mode):
+        _check(lib().crkdg_set_limit_mode(self.ctx, int(mode)))
+
+    def get_limit_mode(self):
+        m = C.c_int()
+        _check(lib().crkdg_get_limit_mode(self.ctx, C.byref(m)))
+        return m.value
 
     def get_launch(self):
         a, b = C.c_int(), C.c_int()

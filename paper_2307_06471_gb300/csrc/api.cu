@@ -77,6 +77,7 @@ struct crkdg_ctx {
     double* d_tab_fe = nullptr;   // forward-Euler tableau (RKDG stages)
     const float* mlp = nullptr;   // learned indicator parameters (device), owned by a crkdg_mlp
     float mlp_zlo = 0.f, mlp_zhi = 0.f;
+    int limit_mode = CRKDG_LIMIT_PASS;   // where a pending limit runs (crkdg_set_limit_mode)
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -162,6 +163,19 @@ int enqueue_reduce(crkdg_ctx* c, int set_dt) {
     return CRKDG_OK;
 }
 
+// the pending limit as an in-place pass over u[cur]; troubled cells are
+// counted into the run state, where the next step's epilogue reports them
+int enqueue_limit_pass(crkdg_ctx* c, double M, int dt_from_dev) {
+    StepArgs a = base_args(c);
+    a.M = M;
+    a.pp_eps = c->pp_pending;
+    a.t = c->t;
+    a.dt_from_dev = dt_from_dev;
+    CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count,
+                           c->stream));
+    return CRKDG_OK;
+}
+
 int enqueue_limit(crkdg_ctx* c, double M) {
     StepArgs a = base_args(c);
     a.M = M;
@@ -197,6 +211,13 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
             a.mlp_zhi = c->mlp_zhi;
             CK(crk::step2d_euler_f32_mlp(c->k, c->basis, a, c->wpb, c->stream));
         } else {
+            if (limit && c->limit_mode == CRKDG_LIMIT_PASS) {
+                // the pending limit as its own in-place pass over u^n; the
+                // step then loads the limited state as it is
+                int r = enqueue_limit_pass(c, M, dt_from_dev);
+                if (r) return r;
+                a.limit = 0;
+            }
             CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
         }
     } else {
@@ -778,6 +799,30 @@ int crkdg_set_launch(crkdg_ctx* c, int seg_rows, int wpb) {
     if (seg_rows > 0) c->seg_rows = std::min(seg_rows, c->mesh.ny);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    return CRKDG_OK;
+}
+
+int crkdg_apply_limit(crkdg_ctx* c) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (c->dim != 2 || !c->pending) return CRKDG_OK;
+    int r = enqueue_limit_pass(c, c->M_pending, c->t_known ? 0 : 1);
+    if (r) return r;
+    c->pending = false;
+    return CRKDG_OK;
+}
+
+int crkdg_set_limit_mode(crkdg_ctx* c, int mode) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (mode != CRKDG_LIMIT_FUSED && mode != CRKDG_LIMIT_PASS) return fail(CRKDG_EINVAL, "unknown limit mode");
+    c->limit_mode = mode;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return CRKDG_OK;
+}
+
+int crkdg_get_limit_mode(const crkdg_ctx* c, int* mode) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (mode) *mode = c->limit_mode;
     return CRKDG_OK;
 }
 

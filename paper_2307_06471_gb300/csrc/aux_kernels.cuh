@@ -139,48 +139,64 @@ __global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict_
 
 // Standalone TVB limiter, in place: a thread reads its own modes and the
 // neighbours' averages (mode 0) and writes only its own modes 1.. , so no
-// thread writes anything another thread reads.  Counts troubled cells.
+// thread writes anything another thread reads.  The x neighbours' averages
+// come from the neighbouring lanes by shuffle (loads only at a warp's ends
+// and at the domain's sides).  Counts troubled cells (one atomic per block).
+// The state's time (for time-dependent ghost averages) comes from the device
+// run state when the run is device driven.  Launched with 128 threads per
+// block along x, one block row per mesh row.
 template <class T, int K, int B, int PHYS>
-__global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned long long* flag_count) {
+__global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __restrict__ u,
+                                                      unsigned long long* flag_count) {
     constexpr int NM = Tab2D<K, B>::NM;
     constexpr int NV = Phys<T, PHYS>::NV;
+    __shared__ unsigned warp_flags[4];
     const int nx = a.nx, ny = a.ny;
     const size_t plane = (size_t)nx * ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    bool fl = false;
-    if (x < nx) {
-        const bool perx = a.bc[0].type == BC_PERIODIC, pery = a.bc[2].type == BC_PERIODIC;
-        T c[NV][NM];
+    const int lane = threadIdx.x & 31;
+    const bool inside = x < nx;
+    const int xc = inside ? x : nx - 1;   // lanes past the east side mirror the last cell (shuffles only)
+    const bool perx = a.bc[0].type == BC_PERIODIC, pery = a.bc[2].type == BC_PERIODIC;
+    const double tl = a.dt_from_dev ? a.ds->t : a.t;
+    T c[NV][NM];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
+    for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int m = 0; m < NM; ++m) c[v][m] = u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x];
-        T own[NV], nb[4][NV];
+        for (int m = 0; m < NM; ++m) c[v][m] = u[(size_t)(v * NM + m) * plane + (size_t)y * nx + xc];
+    T own[NV], nbW[NV], nbE[NV], nbS[NV], nbN[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) own[v] = c[v][0];
-        const int xx[4] = {x - 1, x + 1, x, x};
-        const int yy[4] = {y, y, y - 1, y + 1};
+    for (int v = 0; v < NV; ++v) {
+        own[v] = c[v][0];
+        nbW[v] = shfl_up(own[v], 1);
+        nbE[v] = shfl_down(own[v], 1);
+    }
+    // average of cell (cx, cy), or the ghost average beyond a non-periodic side
+    auto neighbour = [&](int side, int cx, int cy, T* out) {
+        const bool outside = side < 2 ? (!perx && (cx < 0 || cx >= nx)) : (!pery && (cy < 0 || cy >= ny));
+        if (outside) {
+            bc_exterior<T, NV>(a.bc[side], side < 2 ? 0 : 1, own, [&](double& xg, double& yg, double& tg) {
+                xg = a.x0 + (cx + 0.5) * a.dx;
+                yg = a.y0 + (cy + 0.5) * a.dy;
+                tg = tl;
+            }, out);
+        } else {
+            cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
+            cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int cx = xx[s], cy = yy[s];
-            const bool out = (s < 2 && !perx && (cx < 0 || cx >= nx)) || (s >= 2 && !pery && (cy < 0 || cy >= ny));
-            if (out) {
-                bc_exterior<T, NV>(a.bc[s], s < 2 ? 0 : 1, own, [&](double& xc, double& yc, double& tc) {
-                    xc = a.x0 + (cx + 0.5) * a.dx;
-                    yc = a.y0 + (cy + 0.5) * a.dy;
-                    tc = a.t;
-                }, nb[s]);
-            } else {
-                cx = (cx + nx) % nx;
-                cy = (cy + ny) % ny;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) nb[s][v] = u[(size_t)(v * NM) * plane + (size_t)cy * nx + cx];
-            }
+            for (int v = 0; v < NV; ++v) out[v] = u[(size_t)(v * NM) * plane + (size_t)cy * nx + cx];
         }
+    };
+    bool fl = false;
+    if (inside) {
+        if (lane == 0 || x == 0) neighbour(0, x - 1, y, nbW);
+        if (lane == 31 || x == nx - 1) neighbour(1, x + 1, y, nbE);
+        neighbour(2, x, y - 1, nbS);
+        neighbour(3, x, y + 1, nbN);
         if (a.M >= 0.0)
-            fl = tvb_limit_cell<T, NV, NM>(c, nb[0], nb[1], nb[2], nb[3], T(a.M * a.dx * a.dx),
-                                           T(a.M * a.dy * a.dy), T(a.gamma));
+            fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, T(a.M * a.dx * a.dx), T(a.M * a.dy * a.dy),
+                                           T(a.gamma));
         bool sc = false;
         if (a.pp_eps > 0.0) sc = positivity_cell<T, NV, NM, K, B>(c, T(a.gamma), T(a.pp_eps));
         if (fl || sc)
@@ -190,7 +206,13 @@ __global__ void limit2d_kernel(const StepArgs a, T* __restrict__ u, unsigned lon
                 for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x] = c[v][m];
     }
     const unsigned b = __ballot_sync(0xffffffffu, fl);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
+    if (lane == 0) warp_flags[threadIdx.x >> 5] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned n = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += warp_flags[w];
+        if (n) atomicAdd(flag_count, (unsigned long long)n);
+    }
 }
 
 // out = alpha * x + beta * y over n elements (RKDG Shu--Osher combinations)

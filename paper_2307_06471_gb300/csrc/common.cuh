@@ -25,6 +25,7 @@ struct DevState {
     unsigned status;          // ST_* bits
     unsigned counter;         // arrival counter of the last-warp reduction
     unsigned long long steps;
+    unsigned long long lim_count;   // cells flagged by a separate limiter pass since the last step
 };
 
 struct BCSide {

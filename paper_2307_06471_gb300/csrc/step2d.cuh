@@ -151,7 +151,9 @@ constexpr size_t mlp_smem_bytes(int nthr) {
     return sizeof(MlpSmem) + (size_t)(nthr / 32) * (32 * MLP_INP + 64) * sizeof(__nv_bfloat16);
 }
 
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, class PV>
+// LIM = false: an instantiation without the limit-on-load code, for steps
+// whose u^n needs no limiting here (none pending, or a separate pass did it).
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, class PV>
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
@@ -280,7 +282,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             }, out);
         }
     };
-    if (a.limit) load_avg(rstart - 1, avg_prev);
+    if (LIM && a.limit) load_avg(rstart - 1, avg_prev);
     const double hh_ = pv.dx() > pv.dy() ? pv.dx() : pv.dy();
     const double mlp_scale = a.M * hh_ * hh_;
 
@@ -299,7 +301,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
             for (int m = 0; m < NM; ++m) un[v][m] = uin[(size_t)(v * NM + m) * plane + cidx];
 
-        if (a.limit) {
+        if (LIM && a.limit) {
             T avg_cur[NV], nbW[NV], nbE[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) avg_cur[v] = un[v][0];
@@ -790,7 +792,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         ds->maxspeed = mx;
 #pragma unroll
         for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
-        ds->troubled = tr;
+        // troubled cells: this step's limit-on-load, else a separate pass over u^n
+        ds->troubled = a.limit ? tr : double(ds->lim_count);
+        ds->lim_count = 0;
         const double tn = t0 + dt;
         ds->t = tn;
         double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
@@ -808,7 +812,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false>
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true>
 __global__ void __launch_bounds__(CRK_STEP_MAXT, CRK_STEP_MINB2) step2d_kernel(const StepArgs a) {
     if constexpr (MLPI) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -819,7 +823,7 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, CRK_STEP_MINB2) step2d_kernel(c
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
     const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};
-    step2d_body<T, K, B, PHYS, COMP, MLPI>(a, pv, gw);
+    step2d_body<T, K, B, PHYS, COMP, MLPI, LIM>(a, pv, gw);
 }
 
 // Batched ensemble: problems of different sizes and domains share the

@@ -54,6 +54,7 @@ def test_batch_equals_single_problem_runs(prec):
         mesh = B.make_mesh(2, nx, ny, box, [B.BC_OUTFLOW] * 4)
         s = B.Solver(mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, P, stream=stream.cuda_stream)
         s.set_launch(seg_rows=8, warps_per_block=4)
+        s.set_limit_mode(B.LIMIT_FUSED)    # the batch kernel limits on load, as the fused step does
         s.project_function(_ic(prim, box))
         s.limit(50.0)
         s.positivity(1e-10)

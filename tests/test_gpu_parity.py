@@ -139,6 +139,54 @@ def test_dmr_boundaries_and_limiter(prec, tol):
     assert gs.troubled_count() > 0
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_limit_pass_equals_fused_limit(prec):
+    """The pending limiter run as a separate in-place pass before the step
+    and run fused into the step's load give the same states (to rounding: the
+    two kernels may fuse multiply-adds differently) and the same troubled
+    counts (eager steps, device-driven steps, captured graphs)."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    bcs, st = _dmr_bcs()
+    nx, ny = 150, 40
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, mode in (("fused", B.LIMIT_FUSED), ("pass", B.LIMIT_PASS), ("apply", B.LIMIT_FUSED)):
+        gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, prec)
+        gs.close()
+        g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32 if prec == "f32" else B.F64,
+                     stream=stream.cuda_stream)
+        g.set_limit_mode(mode)
+        assert g.get_limit_mode() == mode
+        g.set_launch(seg_rows=7)
+        g.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+        g.limit(50.0)
+        g.positivity(1e-10)
+        counts = []
+        for _ in range(3):
+            dt = g.cfl_dt(0.16)
+            if name == "apply":
+                g.apply_limit()        # the pending limit now; the step then loads u^n as it is
+            g.step(dt)
+            counts.append(g.troubled_count())
+        for cap in (False, True, False):
+            if name == "apply":
+                g.apply_limit()        # device-driven run: the pass reads the state's time on the device
+            g.advance(4, 0.16, 0.2, capture=cap)
+            counts.append(g.troubled_count())
+        out[name] = (g.get_state(), g.time(), counts)
+        assert g.sync() == (0, 0)
+    a = out["fused"]
+    tol = 1e-6 if prec == "f32" else 1e-11
+    for name in ("pass", "apply"):
+        b = out[name]
+        assert np.max(np.abs(a[0] - b[0])) <= tol * np.max(np.abs(a[0])), name
+        assert a[1] == pytest.approx(b[1], rel=tol), name
+        assert a[2] == b[2], (name, a[2], b[2])
+    assert min(a[2]) > 0
+
+
 def test_limiter_alone_matches_oracle_flags():
     nx, ny = 50, 40
     gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f64")
