@@ -5,6 +5,11 @@
 #include "common.cuh"
 #include "limiter.cuh"
 
+// resident blocks per SM the limiter pass is compiled for (tuning knob)
+#ifndef CRK_LIMIT_MINB
+#define CRK_LIMIT_MINB 8
+#endif
+
 namespace crk {
 
 // max_K wave speed (2D: s_x/dx + s_y/dy; 1D: |f'|/dx) and sum_K |K| ubar_K,
@@ -141,16 +146,16 @@ __global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict_
 // neighbours' averages (mode 0) and writes only its own modes 1.. , so no
 // thread writes anything another thread reads.  The x neighbours' averages
 // come from the neighbouring lanes by shuffle (loads only at a warp's ends
-// and at the domain's sides).  Counts troubled cells (one atomic per block).
+// and at the domain's sides).  Counts troubled cells (one atomic per warp
+// that has any).
 // The state's time (for time-dependent ghost averages) comes from the device
 // run state when the run is device driven.  Launched with 128 threads per
 // block along x, one block row per mesh row.
 template <class T, int K, int B, int PHYS>
-__global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __restrict__ u,
-                                                      unsigned long long* flag_count) {
+__global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
+                                                                      unsigned long long* flag_count) {
     constexpr int NM = Tab2D<K, B>::NM;
     constexpr int NV = Phys<T, PHYS>::NV;
-    __shared__ unsigned warp_flags[4];
     const int nx = a.nx, ny = a.ny;
     const size_t plane = (size_t)nx * ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,7 +164,6 @@ __global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __res
     const bool inside = x < nx;
     const int xc = inside ? x : nx - 1;   // lanes past the east side mirror the last cell (shuffles only)
     const bool perx = a.bc[0].type == BC_PERIODIC, pery = a.bc[2].type == BC_PERIODIC;
-    const double tl = a.dt_from_dev ? a.ds->t : a.t;
     T c[NV][NM];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __res
             bc_exterior<T, NV>(a.bc[side], side < 2 ? 0 : 1, own, [&](double& xg, double& yg, double& tg) {
                 xg = a.x0 + (cx + 0.5) * a.dx;
                 yg = a.y0 + (cy + 0.5) * a.dy;
-                tg = tl;
+                tg = a.dt_from_dev ? a.ds->t : a.t;
             }, out);
         } else {
             cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
@@ -194,11 +198,15 @@ __global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __res
         if (lane == 31 || x == nx - 1) neighbour(1, x + 1, y, nbE);
         neighbour(2, x, y - 1, nbS);
         neighbour(3, x, y + 1, nbN);
-        if (a.M >= 0.0)
-            fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, T(a.M * a.dx * a.dx), T(a.M * a.dy * a.dy),
-                                           T(a.gamma));
+        T Mdx2, Mdy2, gam, ppe;
+        if constexpr (sizeof(T) == 4) {
+            Mdx2 = a.Mdx2f; Mdy2 = a.Mdy2f; gam = a.gammaf; ppe = a.pp_epsf;
+        } else {
+            Mdx2 = a.M * a.dx * a.dx; Mdy2 = a.M * a.dy * a.dy; gam = a.gamma; ppe = a.pp_eps;
+        }
+        if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam);
         bool sc = false;
-        if (a.pp_eps > 0.0) sc = positivity_cell<T, NV, NM, K, B>(c, T(a.gamma), T(a.pp_eps));
+        if (a.pp_on) sc = positivity_cell<T, NV, NM, K, B>(c, gam, ppe);
         if (fl || sc)
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -206,13 +214,7 @@ __global__ void __launch_bounds__(128) limit2d_kernel(const StepArgs a, T* __res
                 for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x] = c[v][m];
     }
     const unsigned b = __ballot_sync(0xffffffffu, fl);
-    if (lane == 0) warp_flags[threadIdx.x >> 5] = __popc(b);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned n = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += warp_flags[w];
-        if (n) atomicAdd(flag_count, (unsigned long long)n);
-    }
+    if (lane == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
 }
 
 // out = alpha * x + beta * y over n elements (RKDG Shu--Osher combinations)

@@ -53,6 +53,10 @@ struct StepArgs {
     double pp_eps;            // > 0: positivity-preserving scaling with this floor
     double gamma;
     double beta[2];
+    // limiter parameters as the one-thread-per-cell limiter pass takes them
+    // (filled by set_limiter_params at its launch)
+    float Mdx2f, Mdy2f, gammaf, pp_epsf;
+    int tvb_on, pp_on;
     const float* mlp;         // learned indicator parameters (device), or null
     float mlp_zlo, mlp_zhi;   // logit band in which the TVB test decides
 };
@@ -187,6 +191,17 @@ __device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T*
         default:
             break;
     }
+}
+
+// FP32 copies and switches of the limiter parameters, so that a kernel with
+// one thread per cell does no FP64 arithmetic for them
+inline void set_limiter_params(StepArgs& a) {
+    a.Mdx2f = (float)(a.M * a.dx * a.dx);
+    a.Mdy2f = (float)(a.M * a.dy * a.dy);
+    a.gammaf = (float)a.gamma;
+    a.pp_epsf = (float)a.pp_eps;
+    a.tvb_on = a.M >= 0.0;
+    a.pp_on = a.pp_eps > 0.0;
 }
 
 // Device tableau buffer: FP64 a (MAXS x MAXS, row-major), b, c, followed by

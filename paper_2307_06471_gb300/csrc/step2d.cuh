@@ -193,8 +193,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const bool has_bcW = !perx && xs == 0;
     const bool has_bcE = !perx && xs + 30 >= nx;
 
-    const int r0 = seg * pv.seg_len();
-    const int r1 = min(r0 + pv.seg_len(), ny);
+    // rows split evenly over the segments (each at most seg_len rows)
+    const int r0 = (int)(((long long)seg * ny) / pv.n_segs());
+    const int r1 = (int)(((long long)(seg + 1) * ny) / pv.n_segs());
     const int rstart = (r0 > 0 || pery) ? r0 - 1 : r0;
     const int rend = (r1 < ny || pery) ? r1 : r1 - 1;
 
@@ -532,23 +533,35 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 for (int p = 0; p < NQ; ++p)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) tWn[p][v] = shfl_down(tW[p][v], 1);
-                if (has_bcW && lane == 0) {
+                // boundary strips: the whole warp forms the exterior states (no
+                // divergent branch), only the lane at the boundary keeps them
+                if (has_bcW) {
+                    const bool edge = lane == 0;
 #pragma unroll
-                    for (int p = 0; p < NQ; ++p)
+                    for (int p = 0; p < NQ; ++p) {
+                        T ext[NV];
                         bc_exterior<T, NV>(a.bc[0], 0, tWn[p], [&](double& x, double& y, double& t) {
                             x = pv.x0();
                             y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
                             t = ti();
-                        }, tE[p]);
-                }
-                if (has_bcE && col == nx - 1) {
+                        }, ext);
 #pragma unroll
-                    for (int p = 0; p < NQ; ++p)
+                        for (int v = 0; v < NV; ++v) tE[p][v] = edge ? ext[v] : tE[p][v];
+                    }
+                }
+                if (has_bcE) {
+                    const bool edge = col == nx - 1;
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p) {
+                        T ext[NV];
                         bc_exterior<T, NV>(a.bc[1], 0, tE[p], [&](double& x, double& y, double& t) {
                             x = pv.x0() + nx * pv.dx();
                             y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
                             t = ti();
-                        }, tWn[p]);
+                        }, ext);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) tWn[p][v] = edge ? ext[v] : tWn[p][v];
+                    }
                 }
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
