@@ -206,6 +206,16 @@ int crkdg_sync(crkdg_ctx* ctx, unsigned* device_status);
 /* Current simulation time (host copy). */
 int crkdg_time(const crkdg_ctx* ctx, double* t);
 
+/* Monitor a device-driven run without stalling it: enqueue on the context
+ * stream a copy of the device run state into out[5] = {t, dt of the next
+ * step, t_end, cfl, maximum wave speed (max_K (|u|+c)/dx + (|v|+c)/dy of the
+ * last step's new averages, eq. (3.4)'s FP64 reduction)}.  out is host
+ * memory owned by the caller; it is written when the stream reaches the copy,
+ * so read it after crkdg_sync (or another synchronisation of the stream).
+ * With page-locked (pinned) memory the call returns at once; with pageable
+ * memory the copy waits for the stream.  Returns EINVAL for null. */
+int crkdg_run_state_async(crkdg_ctx* ctx, double* out);
+
 /* Launch shape of the fused 2D step: rows per warp segment and warps per
  * block (0 = keep).  crkdg_autotune times candidates on the current state
  * (state restored afterwards) and keeps the fastest; returns its time/step

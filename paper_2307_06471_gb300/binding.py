@@ -71,6 +71,7 @@ _SIGS = {
     "crkdg_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "crkdg_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "crkdg_set_limit_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "crkdg_run_state_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "crkdg_apply_limit": (C.c_int, [C.c_void_p]),
     "crkdg_get_limit_mode": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "crkdg_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -280,6 +281,12 @@ class Solver:
 
     def apply_limit(self):
         _check(lib().crkdg_apply_limit(self.ctx))
+
+    def run_state_async(self, out_ptr):
+        """Enqueue a copy of {t, dt, t_end, cfl, max wave speed} into the 5
+        doubles at host address out_ptr (pinned memory for an asynchronous
+        copy); read them after sync()."""
+        _check(lib().crkdg_run_state_async(self.ctx, C.c_void_p(out_ptr)))
 
     def set_limit_mode(self, mode):
         _check(lib().crkdg_set_limit_mode(self.ctx, int(mode)))

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -784,6 +785,13 @@ int crkdg_time(const crkdg_ctx* cc, double* t) {
         c->t_known = true;
     }
     *t = c->t;
+    return CRKDG_OK;
+}
+
+int crkdg_run_state_async(crkdg_ctx* c, double* out) {
+    if (check_ctx(c) || !out) return fail(CRKDG_EINVAL, "null argument");
+    static_assert(offsetof(DevState, maxspeed) == 4 * sizeof(double), "run state layout");
+    CK(cudaMemcpyAsync(out, c->d_state, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return CRKDG_OK;
 }
 

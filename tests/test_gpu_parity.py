@@ -187,6 +187,37 @@ def test_limit_pass_equals_fused_limit(prec):
     assert min(a[2]) > 0
 
 
+def test_run_state_async_follows_device_driven_steps():
+    """crkdg_run_state_async copies {t, dt, t_end, cfl, max wave speed} of the
+    device run state into pinned host memory in stream order: after each
+    device-driven step t grows by the dt the previous copy reported, dt is
+    cfl / max wave speed, and the last copy agrees with crkdg_time."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    bcs, st = _dmr_bcs()
+    stream = torch.cuda.Stream()
+    gs, dg = make_pair_2d(96, 24, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, "f32")
+    gs.close()
+    g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32, stream=stream.cuda_stream)
+    g.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    g.limit(50.0)
+    g.positivity(1e-10)
+    g.advance(2, 0.16, 0.2)
+    n = 4
+    buf = torch.zeros(n, 5, dtype=torch.float64, pin_memory=True)
+    for i in range(n):
+        g.step_device()
+        g.run_state_async(buf[i].data_ptr())
+    assert g.sync() == (0, 0)
+    r = buf.numpy()
+    for i in range(1, n):
+        assert r[i, 0] == r[i - 1, 0] + r[i - 1, 1]
+    assert np.all(r[:, 2] == 0.2) and np.all(r[:, 3] == 0.16)
+    assert np.allclose(r[:, 1], 0.16 / r[:, 4], rtol=1e-15, atol=0)
+    assert r[-1, 0] == g.time()
+
+
 def test_limiter_alone_matches_oracle_flags():
     nx, ny = 50, 40
     gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f64")
