@@ -111,6 +111,7 @@ StepArgs base_args(const crkdg_ctx* c) {
         for (int j = 0; j < 16; ++j) a.bc[s].p[j] = c->mesh.bc_params[s][j];
         for (int j = 0; j < 4; ++j) a.bc[s].pf[j] = (float)a.bc[s].p[j];
     }
+    crk::set_bc_affine(a.bc, c->nv);
     a.gamma = c->gamma;
     a.beta[0] = c->beta[0];
     a.beta[1] = c->beta[1];

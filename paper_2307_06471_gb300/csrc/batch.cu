@@ -114,6 +114,7 @@ StepArgs batch_args(const crkdg_batch* b) {
     a.s = b->tab.s;
     a.tab = b->d_tab;
     for (int s = 0; s < 4; ++s) a.bc[s].type = b->bc[s];
+    crk::set_bc_affine(a.bc, 4);
     a.gamma = b->gamma;
     a.seg_len = b->seg_rows;
     a.partials = b->d_partials;

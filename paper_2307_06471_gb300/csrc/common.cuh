@@ -33,6 +33,13 @@ struct BCSide {
     int fn;
     double p[16];
     float pf[4];              // FP32 copy of p[0..3] (the constant exterior state of FN_CONST)
+    // affine form u_ext = m * u_int + c of the sides whose exterior state
+    // depends on nothing else (outflow, reflecting wall, constant state);
+    // affine = 0: the general function (set_bc_affine fills these)
+    int affine;
+    float m[4];
+    float cf[4];
+    double cd[4];
 };
 
 struct StepArgs {
@@ -190,6 +197,25 @@ __device__ __forceinline__ void bc_exterior(const BCSide& bc, int axis, const T*
         } break;
         default:
             break;
+    }
+}
+
+// Affine forms of the boundary sides (see BCSide); the kernels fall back to
+// bc_exterior where affine is 0.
+inline void set_bc_affine(BCSide* bc, int nv) {
+    for (int s = 0; s < 4; ++s) {
+        BCSide& b = bc[s];
+        b.affine = 0;
+        for (int v = 0; v < 4; ++v) { b.m[v] = 1.f; b.cf[v] = 0.f; b.cd[v] = 0.0; }
+        if (b.type == BC_OUTFLOW) {
+            b.affine = 1;
+        } else if (b.type == BC_REFLECT) {
+            b.affine = 1;
+            if (nv >= 3) b.m[1 + (s < 2 ? 0 : 1)] = -1.f;
+        } else if (b.type == BC_DIRICHLET && b.fn == FN_CONST) {
+            b.affine = 1;
+            for (int v = 0; v < 4; ++v) { b.m[v] = 0.f; b.cf[v] = (float)b.p[v]; b.cd[v] = b.p[v]; }
+        }
     }
 }
 

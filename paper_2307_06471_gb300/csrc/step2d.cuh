@@ -537,30 +537,52 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 // divergent branch), only the lane at the boundary keeps them
                 if (has_bcW) {
                     const bool edge = lane == 0;
+                    const BCSide& bcw = a.bc[0];
+                    if (bcw.affine) {
 #pragma unroll
-                    for (int p = 0; p < NQ; ++p) {
-                        T ext[NV];
-                        bc_exterior<T, NV>(a.bc[0], 0, tWn[p], [&](double& x, double& y, double& t) {
-                            x = pv.x0();
-                            y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
-                            t = ti();
-                        }, ext);
+                        for (int p = 0; p < NQ; ++p)
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) tE[p][v] = edge ? ext[v] : tE[p][v];
+                            for (int v = 0; v < NV; ++v) {
+                                const T ext = fma(T(bcw.m[v]), tWn[p][v], sizeof(T) == 4 ? T(bcw.cf[v]) : T(bcw.cd[v]));
+                                tE[p][v] = edge ? ext : tE[p][v];
+                            }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NQ; ++p) {
+                            T ext[NV];
+                            bc_exterior<T, NV>(bcw, 0, tWn[p], [&](double& x, double& y, double& t) {
+                                x = pv.x0();
+                                y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                                t = ti();
+                            }, ext);
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) tE[p][v] = edge ? ext[v] : tE[p][v];
+                        }
                     }
                 }
                 if (has_bcE) {
                     const bool edge = col == nx - 1;
+                    const BCSide& bce = a.bc[1];
+                    if (bce.affine) {
 #pragma unroll
-                    for (int p = 0; p < NQ; ++p) {
-                        T ext[NV];
-                        bc_exterior<T, NV>(a.bc[1], 0, tE[p], [&](double& x, double& y, double& t) {
-                            x = pv.x0() + nx * pv.dx();
-                            y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
-                            t = ti();
-                        }, ext);
+                        for (int p = 0; p < NQ; ++p)
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) tWn[p][v] = edge ? ext[v] : tWn[p][v];
+                            for (int v = 0; v < NV; ++v) {
+                                const T ext = fma(T(bce.m[v]), tE[p][v], sizeof(T) == 4 ? T(bce.cf[v]) : T(bce.cd[v]));
+                                tWn[p][v] = edge ? ext : tWn[p][v];
+                            }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NQ; ++p) {
+                            T ext[NV];
+                            bc_exterior<T, NV>(bce, 0, tE[p], [&](double& x, double& y, double& t) {
+                                x = pv.x0() + nx * pv.dx();
+                                y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                                t = ti();
+                            }, ext);
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) tWn[p][v] = edge ? ext[v] : tWn[p][v];
+                        }
                     }
                 }
 #pragma unroll
