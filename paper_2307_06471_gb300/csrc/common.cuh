@@ -145,6 +145,15 @@ __device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const 
     for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
 }
 
+// The Lax--Friedrichs flux of llf from states whose normal fluxes and wave
+// speeds are already known (the same arithmetic as llf).
+template <class T, int NV>
+__device__ __forceinline__ void lf_from_fluxes(const T* uL, const T* fL, T sL, const T* uR, const T* fR, T sR, T* F) {
+    const T al = sL > sR ? sL : sR;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+}
+
 // Value of the sine boundary data (FN_SINE, FN_SINE_PROD); kept out of line
 // so that the double-precision sines are not inlined at every call site.
 static __device__ __noinline__ double bc_sine_value(int prod, double p0, double p1, double p2, double p3, double p4,

@@ -30,6 +30,14 @@
 #ifndef CRK_V_SMEM
 #define CRK_V_SMEM 0
 #endif
+// 1: stages with a local operator form the east/south Lax--Friedrichs fluxes
+// from the physical fluxes that operator already computed (own traces), the
+// neighbouring lane's (shuffle) and the row below's (kept in shared memory).
+// Off: measured slower (fewer instructions, more shuffle and shared-memory
+// latency in the inner loop: 0.269 against 0.260 ms per step kernel)
+#ifndef CRK_LF_REUSE
+#define CRK_LF_REUSE 0
+#endif
 // launch bounds of the single-problem step kernel (tuning knobs)
 #ifndef CRK_STEP_MAXT
 #define CRK_STEP_MAXT 256
@@ -65,10 +73,11 @@ struct Step2D {
     static constexpr int NRED = NV + 2;   // reduction slots: maxspeed, sums[NV], troubled
 
     // T elements of private shared memory per thread for s stages: L_j
-    // (j < s-1), north traces per stage, pending update, and (CRK_V_SMEM) the
-    // row's sum_i b_i vol_i
+    // (j < s-1), north traces per stage, pending update, (CRK_V_SMEM) the
+    // row's sum_i b_i vol_i, and (CRK_LF_REUSE) the north traces' normal
+    // fluxes and wave speeds per stage
     static __host__ __device__ constexpr int smem_per_thread(int s) {
-        return (s - 1) * NDOF + s * NQ * NV + NDOF + (CRK_V_SMEM ? NDOF : 0);
+        return (s - 1) * NDOF + s * NQ * NV + NDOF + (CRK_V_SMEM ? NDOF : 0) + (CRK_LF_REUSE ? s * NQ * (NV + 1) : 0);
     }
 };
 
@@ -168,6 +177,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const int offN = (S - 1) * C::NDOF;
     const int offP = offN + S * NQ * NV;
     const int offV = offP + C::NDOF;
+    const int offNF = offV + (CRK_V_SMEM ? C::NDOF : 0);   // north fluxes + speeds (CRK_LF_REUSE)
     auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
 
     const int lane = tid & 31;
@@ -483,6 +493,17 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     tE[p][v] = e; tW[p][v] = ww; tN[p][v] = n; tS[p][v] = s;
                 }
             }
+            // east/south Lax--Friedrichs fluxes formed inside the local operator's
+            // point loop (boundary strips and rows keep the separate path below)
+            const bool fuseE = CRK_LF_REUSE && need_L && need_flux && out_row && !has_bcW && !has_bcE;
+            const bool fuseS = CRK_LF_REUSE && need_L && need_flux && do_south && !south_bc;
+            T tWn[NQ][NV];
+            if (fuseE) {
+#pragma unroll
+                for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) tWn[p][v] = shfl_down(tW[p][v], 1);
+            }
             // local operator L_i = cm (face_loc - vol), eq. (2.7)
             if (need_L) {
                 T floc[NV][NM];
@@ -493,10 +514,36 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T fe[NV], fw[NV], fn[NV], fs[NV];
-                    ph.template fluxn<0>(tE[p], fe);
-                    ph.template fluxn<0>(tW[p], fw);
-                    ph.template fluxn<1>(tN[p], fn);
-                    ph.template fluxn<1>(tS[p], fs);
+                    const T sE = ph.template fluxn<0>(tE[p], fe);
+                    const T sW = ph.template fluxn<0>(tW[p], fw);
+                    const T sN = ph.template fluxn<1>(tN[p], fn);
+                    const T sS = ph.template fluxn<1>(tS[p], fs);
+                    if (fuseE) {   // own east trace vs. the right lane's west trace
+                        T fwn[NV], F[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) fwn[v] = shfl_down(fw[v], 1);
+                        const T sWn = shfl_down(sW, 1);
+                        lf_from_fluxes<T, NV>(tE[p], fe, sE, tWn[p], fwn, sWn, F);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) FE[p][v] += bi * F[v];
+                    }
+                    if (fuseS) {   // the row below's north trace vs. own south trace
+                        T lo[NV], flo[NV], F[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            lo[v] = slot(offN + (i * NQ + p) * NV + v);
+                            flo[v] = slot(offNF + (i * NQ + p) * (NV + 1) + v);
+                        }
+                        const T slo = slot(offNF + (i * NQ + p) * (NV + 1) + NV);
+                        lf_from_fluxes<T, NV>(lo, flo, slo, tS[p], fs, sS, F);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) FS[p][v] += bi * F[v];
+                    }
+                    if (CRK_LF_REUSE && keep_north) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) slot(offNF + (i * NQ + p) * (NV + 1) + v) = fn[v];
+                        slot(offNF + (i * NQ + p) * (NV + 1) + NV) = sN;
+                    }
                     if constexpr (NV % 2 == 0) {
 #pragma unroll
                         for (int v = 0; v < NV; v += 2) {
@@ -527,8 +574,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             }
             if (!need_flux) continue;
             // east face: own east trace vs. the west trace of the lane to the right
-            if (out_row) {
-                T tWn[NQ][NV];
+            if (out_row && !fuseE) {
 #pragma unroll
                 for (int p = 0; p < NQ; ++p)
 #pragma unroll
@@ -594,7 +640,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 }
             }
             // south face: north trace of the row below (stored) vs. own south trace
-            if (do_south) {
+            if (do_south && !fuseS) {
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T lo[NV];
