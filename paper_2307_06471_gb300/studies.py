@@ -389,9 +389,58 @@ def advection2d_inflow(sizes=(10, 20, 40, 80), T=0.4, k=3, basis="Q"):
     return {"study": "advection2d_inflow", "k": k, "basis": basis, "T": T, "rows": rows}
 
 
+def advection_hbm(N=4096, steps=200, k=2, basis="Q"):
+    """2D linear advection u_t + u_x + 0.5 u_y = 0, periodic [0,1]^2, Q^2,
+    SSP-RK3, FP32, N x N cells (4096^2: 151M DOF, 604 MB per state copy, far
+    above L2): the fused step with a trivial flux, measured against both
+    rooflines -- HBM (u^n read + u^{n+1} written per step) and FP32."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    from paper_2307_06471_gb300.workcount import step_bytes_per_cell, step_flops_per_cell
+    build.build()
+    stream = torch.cuda.Stream()
+    mesh = B.make_mesh(2, N, N, (0.0, 1.0, 0.0, 1.0), [B.BC_PERIODIC] * 4)
+    s = B.Solver(mesh, k, B.BASIS_Q if basis == "Q" else B.BASIS_P, GTB.SSPRK3, B.ADVECTION, B.F32,
+                 beta=(1.0, 0.5), stream=stream.cuda_stream)
+    s.project_function(lambda X, Y: (np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y))[..., None])
+    h = 1.0 / N
+    dt = 0.1 / (1.0 / h + 0.5 / h)
+    for _ in range(5):
+        s.step(dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(dt)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cells = N * N
+    nm = len(_modes(k, basis))
+    A, b = GTB.SSPRK3
+    fpc = step_flops_per_cell(k, basis, "advection", A, b)
+    bpc = step_bytes_per_cell(k, basis, "advection", 4)
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                        "MEASURED_PEAKS.json")))
+    hbm_peak = float(peaks.get("hbm_gbs", 6796.5))
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    gbs = bpc * cells / (ms * 1e-3) / 1e9
+    tf = fpc * cells / (ms * 1e-3) / 1e12
+    code, status = s.sync()
+    s.close()
+    return {"study": "advection_hbm", "N": N, "k": k, "basis": basis, "steps": steps, "ms_per_step": ms,
+            "dof_updates_per_s": cells * nm * steps / (ms * steps * 1e-3), "bytes_per_cell": bpc,
+            "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / hbm_peak, "flop_per_cell": fpc,
+            "tflops": tf, "fp32_frac": tf / fp32_peak, "status": status}
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d"])
+    ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d",
+                                     "advection_hbm"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -408,6 +457,8 @@ if __name__ == "__main__":
         r = advection1d()
     elif a.study == "advection2d":
         r = advection2d_inflow()
+    elif a.study == "advection_hbm":
+        r = advection_hbm()
     else:
         r = ensemble(a.n, a.steps, a.precision)
     print(json.dumps(r, default=float))
