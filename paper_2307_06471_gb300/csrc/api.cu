@@ -144,14 +144,22 @@ int max_wpb(crkdg_ctx* c) {
 int default_launch(crkdg_ctx* c) {
     if (c->dim != 2) return CRKDG_OK;
     const int ns = (c->mesh.nx + 29) / 30;
-    // about 8 resident warps on each of the 152 SMs, segments of >= 8 rows
-    const long target = 152L * 8;
-    int L = (int)std::max(8L, ((long)ns * c->mesh.ny + target - 1) / target);
-    L = std::min(L, c->mesh.ny);
-    c->seg_rows = L;
     int w = max_wpb(c);
     if (w < 0) return w;
     c->wpb = std::min(w, 4);
+    // one wave: as many warps as the 152 SMs hold at once (registers and
+    // private shared memory of the step kernel decide), segments of >= 8 rows
+    crk::KernelInfo ki;
+    CK(crk::info_step2d(c->kphys, c->precision, c->k, c->basis, c->tab.s, &ki));
+    const int regs_warp = ((ki.regs + 7) / 8) * 8 * 32;
+    const int by_regs = 65536 / regs_warp;
+    const int by_smem = (228 * 1024) / std::max(1, ki.smem_per_thread * 32);
+    int resident = std::min(64, std::min(by_regs, by_smem));
+    resident = std::max(c->wpb, resident / c->wpb * c->wpb);
+    const long target = 152L * resident;
+    const long nseg = std::max(1L, target / ns);
+    int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
+    c->seg_rows = std::min(L, c->mesh.ny);
     return CRKDG_OK;
 }
 

@@ -45,6 +45,11 @@
 #ifndef CRK_STEP_MINB2
 #define CRK_STEP_MINB2 1
 #endif
+// blocks per SM the scalar (advection) step is compiled for: its live state
+// is a quarter of the Euler step's, so it can trade registers for warps
+#ifndef CRK_STEP_MINB_ADV
+#define CRK_STEP_MINB_ADV 2
+#endif
 
 namespace crk {
 
@@ -894,7 +899,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
 template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true>
-__global__ void __launch_bounds__(CRK_STEP_MAXT, CRK_STEP_MINB2) step2d_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MINB_ADV : CRK_STEP_MINB2)
+    step2d_kernel(const StepArgs a) {
     if constexpr (MLPI) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
         MlpSmem& mw = *reinterpret_cast<MlpSmem*>(smem_raw + mlp_smem_offset<T, K, B, PHYS>(a.s, blockDim.x));
