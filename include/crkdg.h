@@ -218,8 +218,9 @@ int crkdg_run_state_async(crkdg_ctx* ctx, double* out);
 
 /* Launch shape of the fused 2D step: rows per warp segment and warps per
  * block (0 = keep).  crkdg_autotune times candidates on the current state
- * (state restored afterwards) and keeps the fastest; returns its time/step
- * in microseconds. */
+ * (run state restored afterwards; a limit pending in CRKDG_LIMIT_PASS mode is
+ * applied first, as the next step would apply it) and keeps the fastest;
+ * returns its time per step kernel in microseconds.  Synchronises. */
 int crkdg_set_launch(crkdg_ctx* ctx, int seg_rows, int warps_per_block);
 int crkdg_get_launch(const crkdg_ctx* ctx, int* seg_rows, int* warps_per_block);
 int crkdg_autotune(crkdg_ctx* ctx, double* best_us);

@@ -185,6 +185,7 @@ class Solver:
         _check(L.crkdg_create(C.byref(mesh), k, basis, FLUX_LLF, C.byref(tab), gamma, physics, precision,
                               _dptr(pp), C.c_void_p(stream) if stream else None, C.byref(self.ctx)))
         self.mesh = mesh
+        self.config = {"k": k, "basis": basis, "stages": tab.s, "physics": physics, "precision": precision}
         nc, nm, nv, nq = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(L.crkdg_sizes(self.ctx, C.byref(nc), C.byref(nm), C.byref(nv), C.byref(nq)))
         self.n_cells, self.n_modes, self.n_vars, self.n_qp = nc.value, nm.value, nv.value, nq.value
@@ -301,9 +302,42 @@ class Solver:
         _check(lib().crkdg_get_launch(self.ctx, C.byref(a), C.byref(b)))
         return a.value, b.value
 
-    def autotune(self):
+    def tune_key(self):
+        """Key of this solver's launch-tuning entry: mesh size, scheme,
+        precision, limit mode and the GPU's name."""
+        import torch
+        c = self.config
+        return "%dx%d/k%d%s/s%d/%s/%s/limit%d/%s" % (
+            self.mesh.nx, self.mesh.ny, c["k"], "PQ"[c["basis"]], c["stages"],
+            "euler" if c["physics"] == EULER else "advection", ("f32", "f64", "f32c")[c["precision"]],
+            self.get_limit_mode(), torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu")
+
+    def autotune(self, cache=None):
+        """Time the step kernel's launch shapes on the current state and keep
+        the fastest (crkdg_autotune); returns microseconds per step kernel.
+        cache: path of a JSON file of earlier results, keyed by tune_key();
+        a hit applies the stored shape without timing, a miss times and
+        stores."""
+        import json
+        import os
+        key = self.tune_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                e = table[key]
+                self.set_launch(e["seg_rows"], e["warps_per_block"])
+                return e["us"]
         us = C.c_double()
         _check(lib().crkdg_autotune(self.ctx, C.byref(us)))
+        if cache:
+            L, W = self.get_launch()
+            table[key] = {"seg_rows": L, "warps_per_block": W, "us": us.value}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
         return us.value
 
     def features(self, X_ptr, y_ptr, M):

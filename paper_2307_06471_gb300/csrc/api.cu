@@ -854,9 +854,21 @@ int crkdg_autotune(crkdg_ctx* c, double* best_us) {
     if (check_ctx(c)) return CRKDG_EINVAL;
     if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "autotune is for the 2D step");
     // time candidate shapes on the current state; u[cur] is only read, the
-    // device run state is saved and restored around the trials
+    // device run state is saved and restored around the trials.  A limit
+    // pending in pass mode is applied first (in place, as the next step
+    // would), so the trials time the step kernel as a pass-mode step runs it
+    if (c->pending && c->limit_mode == CRKDG_LIMIT_PASS) {
+        if (!c->t_known) {
+            CK(cudaMemcpy(&c->t, &c->d_state->t, sizeof(double), cudaMemcpyDeviceToHost));
+            c->t_known = true;
+        }
+        int r = enqueue_limit_pass(c, c->M_pending, 0);
+        if (r) return r;
+        c->pending = false;
+    }
     DevState saved;
-    CK(cudaMemcpy(&saved, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&saved, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     const int mx = max_wpb(c);
     if (mx < 0) return mx;
     const int rows[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96};

@@ -218,6 +218,41 @@ def test_run_state_async_follows_device_driven_steps():
     assert r[-1, 0] == g.time()
 
 
+def test_autotune_keeps_the_state_and_caches(tmp_path):
+    """crkdg_autotune with a limit pending (pass mode) leaves the run as it
+    was: the next step of the tuned solver equals an untouched twin's bit for
+    bit (launch shapes do not change results), troubled counts included; the
+    JSON cache gives a second solver the same shape without timing."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    bcs, st = _dmr_bcs()
+    stream = torch.cuda.Stream()
+
+    def make():
+        gs, dg = make_pair_2d(150, 40, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, "f32")
+        gs.close()
+        g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32, stream=stream.cuda_stream)
+        g.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+        g.limit(50.0)
+        g.positivity(1e-10)
+        g.advance(3, 0.16, 0.2)
+        return g
+
+    a, b = make(), make()
+    cache = str(tmp_path / "tune.json")
+    assert a.autotune(cache=cache) > 0
+    for g in (a, b):
+        g.step(g.cfl_dt(0.16))
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.troubled_count() == b.troubled_count() > 0
+    assert a.time() == b.time()
+    c = make()
+    c.set_launch(5, 1)
+    c.autotune(cache=cache)
+    assert c.get_launch() == a.get_launch()
+
+
 def test_limiter_alone_matches_oracle_flags():
     nx, ny = 50, 40
     gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), 2, "P", "euler", "ssprk3", PER, "f64")
