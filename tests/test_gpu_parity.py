@@ -101,6 +101,29 @@ def test_advection_with_inflow_boundaries_f64(k, basis):
     assert rel_err(from_planes(gs.get_state()), w) < 1e-12
 
 
+@pytest.mark.parametrize("k,basis,launch", [(0, "P", None), (1, "P", (9, 2)), (2, "Q", None), (2, "P", (9, 4)),
+                                            (3, "Q", None)])
+def test_advection_f32_matches_oracle(k, basis, launch):
+    """The FP32 scalar step (compiled for two blocks per SM) against the
+    FP64 oracle: periodic linear advection, five SSP-RK3 steps, on a mesh of
+    ragged strips and segments, with the residency-based default launch shape
+    or a fixed one."""
+    nx, ny = 301, 203
+    gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), k, basis, "advection", "ssprk3", PER, "f32", beta=(1.0, 0.5))
+    if launch:
+        gs.set_launch(*launch)
+    u = inp.random_modal_state(ny, nx, k, basis, "advection", seed=21)
+    u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
+    gs.set_state(to_planes(u), 0.0)
+    dt = 0.2 / (nx + 0.5 * ny)
+    w, t = u.copy(), 0.0
+    for _ in range(5):
+        gs.step(dt)
+        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3)
+        t += dt
+    assert rel_err(from_planes(gs.get_state()), w) < 1e-5
+
+
 def _dmr_bcs():
     st = inp.dmr_states()
     post, pre = list(st["post"]), list(st["pre"])
