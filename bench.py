@@ -363,12 +363,12 @@ def main():
         wall = time.perf_counter() - t0
         assert code2 == 0 and bool((mon[:, 1] > 0).all())
         e2e = {"value": ws * dof * args.steps / wall, "unit": UNIT,
-               "h2d_bytes_per_step": (host.nbytes // 2) // args.steps,
-               "d2h_bytes_per_step": 40 + (out.nbytes // 2) // args.steps,
-               "note": "FP64 host state converted to FP32 and uploaded once, device-driven steps "
+               "h2d_bytes_per_step": host.nbytes // args.steps,
+               "d2h_bytes_per_step": 40 + out.nbytes // args.steps,
+               "note": "FP64 host state uploaded once (rounded to FP32 on the GPU), device-driven steps "
                        "(crkdg_step_device), the run state (t, dt, max wave speed) read back every step "
-                       "into pinned memory, state downloaded once; bytes counted as transferred "
-                       "(FP32 on the link)"}
+                       "into pinned memory, state downloaded once (widened to FP64 on the GPU); bytes "
+                       "per step = transfers / steps"}
         s2.close()
 
     cpu = None

@@ -135,7 +135,10 @@ int crkdg_quadrature_points(const crkdg_ctx* ctx, double* xy);
 int crkdg_project_ic(crkdg_ctx* ctx, const double* values);
 
 /* Replace / read the state, host FP64 planes [v][m][y][x].  get_state first
- * applies a pending limit (see crkdg_limit).  Both synchronise. */
+ * applies a pending limit (see crkdg_limit).  FP32 states travel as FP64 and
+ * are rounded (set) or widened (get) on the GPU, through a staging buffer of
+ * the state's size in FP64 that the context allocates on first use (ENOMEM if
+ * it cannot).  Both synchronise. */
 int crkdg_set_state(crkdg_ctx* ctx, const double* host_state, double t);
 int crkdg_get_state(crkdg_ctx* ctx, double* host_state);
 

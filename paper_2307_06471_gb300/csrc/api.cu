@@ -79,6 +79,7 @@ struct crkdg_ctx {
     const float* mlp = nullptr;   // learned indicator parameters (device), owned by a crkdg_mlp
     float mlp_zlo = 0.f, mlp_zhi = 0.f;
     int limit_mode = CRKDG_LIMIT_PASS;   // where a pending limit runs (crkdg_set_limit_mode)
+    double* d_stage = nullptr;            // FP64 staging of state I/O for FP32 states (first use)
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -365,6 +366,7 @@ void crkdg_destroy(crkdg_ctx* c) {
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->u3) cudaFree(c->u3);
+    if (c->d_stage) cudaFree(c->d_stage);
     if (c->d_tab_fe) cudaFree(c->d_tab_fe);
     delete c;
 }
@@ -424,12 +426,13 @@ int crkdg_set_state(crkdg_ctx* c, const double* h, double t) {
     if (c->precision == CRKDG_F64) {
         CK(cudaMemcpyAsync(c->u[c->cur], h, c->elems * 8, cudaMemcpyHostToDevice, c->stream));
     } else {
-        std::vector<float> f(c->elems * c->planes);
-        for (size_t i = 0; i < c->elems; ++i) {
-            f[i] = (float)h[i];
-            if (c->planes == 2) f[c->elems + i] = (float)(h[i] - (double)f[i]);
+        // FP64 over the link, rounded to the FP32 state on the GPU
+        if (!c->d_stage && cudaMalloc(&c->d_stage, c->elems * 8) != cudaSuccess) {
+            c->d_stage = nullptr;
+            return fail(CRKDG_ENOMEM, "cudaMalloc of the state staging buffer failed");
         }
-        CK(cudaMemcpyAsync(c->u[c->cur], f.data(), f.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->d_stage, h, c->elems * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(crk::launch_f64_to_f32(c->d_stage, static_cast<float*>(c->u[c->cur]), c->elems, c->planes == 2, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     c->t = t;
@@ -456,10 +459,15 @@ int crkdg_get_state(crkdg_ctx* c, double* h) {
         CK(cudaMemcpyAsync(h, c->u[c->cur], c->elems * 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {
-        std::vector<float> f(c->elems * c->planes);
-        CK(cudaMemcpyAsync(f.data(), c->u[c->cur], f.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        // widened to FP64 on the GPU, FP64 over the link
+        if (!c->d_stage && cudaMalloc(&c->d_stage, c->elems * 8) != cudaSuccess) {
+            c->d_stage = nullptr;
+            return fail(CRKDG_ENOMEM, "cudaMalloc of the state staging buffer failed");
+        }
+        CK(crk::launch_f32_to_f64(static_cast<const float*>(c->u[c->cur]), c->d_stage, c->elems, c->planes == 2,
+                                  c->stream));
+        CK(cudaMemcpyAsync(h, c->d_stage, c->elems * 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < c->elems; ++i) h[i] = c->planes == 2 ? (double)f[i] + (double)f[c->elems + i] : f[i];
     }
     return CRKDG_OK;
 }

@@ -136,7 +136,32 @@ cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, doub
 
 namespace {
 __global__ void set_time_kernel(DevState* ds, double t) { ds->t = t; }
+
+// round to nearest; comp: lo = the rounding remainder, also rounded
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n, int comp) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = in[i];
+        const float hi = __double2float_rn(x);
+        out[i] = hi;
+        if (comp) out[n + i] = __double2float_rn(x - (double)hi);
+    }
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, size_t n, int comp) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = comp ? (double)in[i] + (double)in[n + i] : (double)in[i];
+}
 }  // namespace
+
+cudaError_t launch_f64_to_f32(const double* in, float* out, size_t n, int comp, cudaStream_t st) {
+    f64_to_f32_kernel<<<8 * 152, 256, 0, st>>>(in, out, n, comp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, int comp, cudaStream_t st) {
+    f32_to_f64_kernel<<<8 * 152, 256, 0, st>>>(in, out, n, comp);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st) {
     set_time_kernel<<<1, 1, 0, st>>>(ds, t);

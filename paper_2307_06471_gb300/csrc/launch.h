@@ -52,6 +52,10 @@ cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, c
 cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,
                          cudaStream_t st);
 cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st);
+// FP64 staging <-> FP32 state of n elements: one plane set (comp = 0) or the
+// compensated hi + lo plane sets (comp = 1, lo at offset n)
+cudaError_t launch_f64_to_f32(const double* in, float* out, size_t n, int comp, cudaStream_t st);
+cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, int comp, cudaStream_t st);
 
 struct BatchProblem;
 #define CRK_DECL_B(NAME)                                                                                     \
