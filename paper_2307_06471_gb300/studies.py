@@ -437,10 +437,67 @@ def advection_hbm(N=4096, steps=200, k=2, basis="Q"):
             "tflops": tf, "fp32_frac": tf / fp32_peak, "status": status}
 
 
+def dmr_full(nx=1920, ny=480, k=2, T=0.2, cfl=None, precision="f32"):
+    """The double Mach reflection run to T = 0.2 (Sec. 4.2): P^k, SSP-RK3,
+    TVB M = 50 + positivity scaling, CFL 0.16 for P^2 and 0.3 for P^1 (the
+    paper's numbers), device-driven steps with the run state (t, dt, max wave
+    speed) read back after every step.  Reports the step count, the whole
+    run's wall time and rate, and the final state's density and pressure
+    ranges (cell averages) and troubled-cell count."""
+    import torch
+    import crkdg_inputs as inp
+    import bench
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import build
+    from paper_2307_06471_gb300 import tableaux as GTB
+    build.build()
+    cfl = cfl or (0.16 if k == 2 else 0.3)
+    stream = torch.cuda.Stream()
+    st = inp.dmr_states()
+    mesh, _ = bench.dmr_mesh(B, inp, nx, ny)
+    s = B.Solver(mesh, k, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32 if precision == "f32" else B.F64,
+                 stream=stream.cuda_stream)
+    s.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    s.limit(50.0)
+    s.positivity(1e-10)
+    cap = 40000
+    mon = torch.zeros(cap, 5, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.advance(1, cfl, T)
+    s.run_state_async(mon[0].data_ptr())
+    n = 1
+    while True:
+        if n % 256 == 0:
+            stream.synchronize()
+            if mon[n - 1, 0] >= T * (1 - 1e-12) or mon[n - 1, 1] <= 0.0:
+                break
+        if n >= cap:
+            break
+        s.step_device()
+        s.run_state_async(mon[n].data_ptr())
+        n += 1
+    code, status = s.sync()
+    wall = time.perf_counter() - t0
+    r = mon[:n].numpy()
+    steps = int(np.count_nonzero(np.concatenate([[1.0], r[:-1, 1]]) > 0.0))
+    troubled = s.troubled_count()
+    u = s.get_state()
+    rho = u[0, 0]
+    mx, my, E = u[1, 0], u[2, 0], u[3, 0]
+    p = 0.4 * (E - 0.5 * (mx * mx + my * my) / rho)
+    nm = u.shape[1]
+    s.close()
+    return {"study": "dmr_full", "mesh": "%dx%d" % (nx, ny), "k": k, "cfl": cfl, "T": float(r[n - 1, 0]),
+            "steps": steps, "wall_s": wall, "dof_updates_per_s": nx * ny * 4 * nm * steps / wall,
+            "status": status, "code": code, "rho_min": float(rho.min()), "rho_max": float(rho.max()),
+            "p_min": float(p.min()), "p_max": float(p.max()), "troubled_last_step": int(troubled)}
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d",
-                                     "advection_hbm"])
+                                     "advection_hbm", "dmr_full"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -459,6 +516,8 @@ if __name__ == "__main__":
         r = advection2d_inflow()
     elif a.study == "advection_hbm":
         r = advection_hbm()
+    elif a.study == "dmr_full":
+        r = dmr_full(*(int(v) for v in a.sizes.split(",")[:3])) if a.sizes != "80,160,320" else dmr_full()
     else:
         r = ensemble(a.n, a.steps, a.precision)
     print(json.dumps(r, default=float))
