@@ -1,0 +1,136 @@
+"""The CUDA path (FP64) on the configurations of the paper's error tables,
+checked against the numbers the paper prints (fixtures under tests/golden/,
+each citing its table), with the agreement bands the oracle's own pins use:
+the GPU's projection, time stepping, dt rule and boundary data all run here;
+only the error norms are evaluated on the host (the oracle's quadrature
+norms, a measurement, not a step of the method).
+
+- Table 4.4 (Sec. 4.1.1): 1D linear advection, P^2, eq. (2.10), dt = 0.16 h,
+  t = 20, periodic and inflow boundaries: values within 1 % (L2) / 2 %
+  (Linf), orders 3 +- 0.05.
+- Table 4.2 (Sec. 4.1.1): 1D Euler, P^1 with eq. (2.9) at CFL 0.3 and P^2
+  with eq. (2.10) at CFL 0.16, t = 2: L2 within 5 %, orders within 0.06.
+- Table 4.5 (Sec. 4.1.2): 2D Euler on rectangles, P^2, eq. (2.10), CFL 0.12,
+  t = 0.5: normalised L2 within 5 %, order 3 +- 0.1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.dg1d import DG1D
+from oracle.dg2d import DG2D
+from oracle.norms import errors_1d, errors_2d
+from oracle.physics import Advection, Euler
+from oracle.problems import euler1d_sine, euler2d_sine, sine_advection
+from tests.pairing import from_planes
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def order(e1, e2):
+    return np.log2(e1 / e2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_06471_gb300 import build
+    build.build()
+
+
+def march(s, T, dt=None, cfl=None):
+    """Fixed dt (last step clipped) or the GPU's CFL dt, to T."""
+    t = 0.0
+    while t < T - 1e-14 * max(1.0, abs(T)):
+        d = dt if dt is not None else s.cfl_dt(cfl)
+        d = min(d, T - t)
+        s.step(d)
+        t += d
+    assert s.sync() == (0, 0)
+    return t
+
+
+def solver_1d(N, L, k, physics, tab, bc):
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    if bc == "periodic":
+        codes = [(B.BC_PERIODIC, 0, None), (B.BC_PERIODIC, 0, None)]
+    else:   # exact data sin(0 - t) at the inflow side, outflow at the other
+        codes = [(B.BC_DIRICHLET, B.FN_SINE, [1.0, 1.0, 0.0, 1.0, 0.0]), (B.BC_OUTFLOW, 0, None)]
+    mesh = B.make_mesh(1, N, 1, (0.0, L, 0.0, 1.0), [codes[0][0], codes[1][0], 0, 0],
+                       [codes[0][1], codes[1][1], 0, 0], [codes[0][2], codes[1][2], None, None])
+    return B.Solver(mesh, k, B.BASIS_P, GTB.BY_NAME[tab], B.EULER if physics == "euler" else B.ADVECTION,
+                    B.F64, beta=(1.0, 0.0))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "inflow"])
+def test_table_4_4_on_gpu(bc):
+    rows = [r for r in golden("table_4_4_boundary_error.txt") if r[0] == "cRKDG" and r[1] == bc]
+    L = 4 * np.pi
+    errs = []
+    for _, _, N, l2, linf in rows:
+        N = int(N)
+        h = L / N
+        nst = int(np.ceil(20.0 / (0.16 * h)))
+        s = solver_1d(N, L, 2, "advection", "heun3", bc)
+        s.project_function(lambda x: sine_advection(x, 0.0))
+        march(s, 20.0, dt=20.0 / nst)
+        dg = DG1D(np.linspace(0, L, N + 1), 2, Advection([1.0]))
+        e = errors_1d(dg, from_planes(s.get_state(), dim=1), lambda x: sine_advection(x, 20.0), nq=10)
+        s.close()
+        errs.append(e)
+        assert e["L2"] == pytest.approx(float(l2), rel=0.01)
+        assert e["Linf"] == pytest.approx(float(linf), rel=0.02)
+    for a, b in zip(errs[:-1], errs[1:]):
+        assert abs(order(a["L2"], b["L2"]) - 3.0) < 0.05
+        assert abs(order(a["Linf"], b["Linf"]) - 3.0) < 0.05
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_table_4_2_on_gpu(k):
+    tab, cfl = ("midpoint", 0.3) if k == 1 else ("heun3", 0.16)
+    rows = [r for r in golden("table_4_2_euler1d.txt") if int(r[0]) == k]
+    errs = []
+    for _, N, l2, _ in rows:
+        N = int(N)
+        s = solver_1d(N, 2.0, k, "euler", tab, "periodic")
+        s.project_function(lambda x: euler1d_sine(x, 0.0))
+        march(s, 2.0, cfl=cfl)
+        dg = DG1D(np.linspace(0, 2, N + 1), k, Euler(1.4, 1))
+        e = errors_1d(dg, from_planes(s.get_state(), dim=1), lambda x: euler1d_sine(x, 2.0))
+        s.close()
+        errs.append(e["L2"])
+        assert e["L2"] == pytest.approx(float(l2), rel=0.05)
+    gold = [float(r[2]) for r in rows]
+    for i in range(len(errs) - 1):
+        assert abs(order(errs[i], errs[i + 1]) - order(gold[i], gold[i + 1])) < 0.06
+
+
+def test_table_4_5_on_gpu():
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    errs = []
+    for _, N, l2 in golden("table_4_5_euler2d_rect.txt"):
+        N = int(N)
+        mesh = B.make_mesh(2, N, N, (0.0, 2.0, 0.0, 2.0), [B.BC_PERIODIC] * 4)
+        s = B.Solver(mesh, 2, B.BASIS_P, GTB.HEUN3, B.EULER, B.F64)
+        s.project_function(lambda X, Y: euler2d_sine(X, Y, 0.0))
+        march(s, 0.5, cfl=0.12)
+        dg = DG2D(N, N, (0, 2, 0, 2), 2, "P", Euler(1.4, 2), {side: "periodic" for side in "WESN"})
+        e = errors_2d(dg, from_planes(s.get_state()), lambda X, Y: euler2d_sine(X, Y, 0.5))["L2"] / 2.0
+        s.close()
+        errs.append(e)
+        assert e == pytest.approx(float(l2), rel=0.05)
+    assert abs(order(*errs) - 3.0) < 0.1
