@@ -242,6 +242,21 @@ enum { CRKDG_LIMIT_FUSED = 0, CRKDG_LIMIT_PASS = 1 };
 int crkdg_set_limit_mode(crkdg_ctx* ctx, int mode);
 int crkdg_get_limit_mode(const crkdg_ctx* ctx, int* mode);
 
+/* How the 2D step evaluates its operators for linear advection.
+ * CRKDG_FORM_AUTO (default): where the flux is linear (CRKDG_ADVECTION, FP32
+ * or FP64) and every non-periodic side is outflow, wall or a constant state,
+ * the step uses the modal form of the operators — the local operator (eq.
+ * (2.7)) is beta . grad of the modal polynomial, the final stage's
+ * sum_i b_i div^DG f(u^(i)) equals the DG operator of sum_i b_i u^(i) (the
+ * linearity behind Theorem 3.3), applied once with the upwind flux — which
+ * the quadrature form computes exactly as well; results agree to rounding.
+ * The modal step takes its own launch shape (crkdg_set_launch and
+ * crkdg_autotune tune the quadrature step).  CRKDG_FORM_QUADRATURE: always
+ * the quadrature form.  EINVAL for another value. */
+enum { CRKDG_FORM_QUADRATURE = 0, CRKDG_FORM_AUTO = 1 };
+int crkdg_set_operator_form(crkdg_ctx* ctx, int form);
+int crkdg_get_operator_form(const crkdg_ctx* ctx, int* form);
+
 /* Apply the pending limiter (2D) to the stored state now, in place on the
  * device, as the separate pass above; async on the context stream.  The next
  * step then loads the state without limiting it again and reports the cells

@@ -24,6 +24,7 @@ ADVECTION, EULER = 0, 1
 BASIS_P, BASIS_Q = 0, 1
 F32, F64, F32C = 0, 1, 2
 LIMIT_FUSED, LIMIT_PASS = 0, 1
+FORM_QUADRATURE, FORM_AUTO = 0, 1
 FLUX_LLF = 0
 ST_NONPHYSICAL, ST_NAN, ST_TIMEOUT = 1, 2, 4
 
@@ -73,6 +74,8 @@ _SIGS = {
     "crkdg_set_limit_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "crkdg_run_state_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "crkdg_apply_limit": (C.c_int, [C.c_void_p]),
+    "crkdg_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
+    "crkdg_get_operator_form": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "crkdg_get_limit_mode": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "crkdg_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_save": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -279,6 +282,14 @@ class Solver:
 
     def set_launch(self, seg_rows=0, warps_per_block=0):
         _check(lib().crkdg_set_launch(self.ctx, int(seg_rows), int(warps_per_block)))
+
+    def set_operator_form(self, form):
+        _check(lib().crkdg_set_operator_form(self.ctx, int(form)))
+
+    def get_operator_form(self):
+        f = C.c_int()
+        _check(lib().crkdg_get_operator_form(self.ctx, C.byref(f)))
+        return f.value
 
     def apply_limit(self):
         _check(lib().crkdg_apply_limit(self.ctx))

@@ -80,6 +80,8 @@ struct crkdg_ctx {
     float mlp_zlo = 0.f, mlp_zhi = 0.f;
     int limit_mode = CRKDG_LIMIT_PASS;   // where a pending limit runs (crkdg_set_limit_mode)
     double* d_stage = nullptr;            // FP64 staging of state I/O for FP32 states (first use)
+    int op_form = CRKDG_FORM_AUTO;        // crkdg_set_operator_form
+    int lin_seg_rows = 0, lin_wpb = 0;    // launch shape of the modal linear step (first use)
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -174,6 +176,44 @@ int enqueue_reduce(crkdg_ctx* c, int set_dt) {
     return CRKDG_OK;
 }
 
+// the modal step applies: linear flux, 2D, FP32/FP64, every non-periodic side
+// affine (outflow, wall, constant state), not switched off
+bool use_linear(const crkdg_ctx* c) {
+    if (c->op_form != CRKDG_FORM_AUTO || c->kphys != crk::PHYS_ADV || c->dim != 2 ||
+        c->precision == CRKDG_F32C)
+        return false;
+    crk::BCSide bc[4];
+    for (int s = 0; s < 4; ++s) {
+        bc[s].type = c->mesh.bc[s];
+        bc[s].fn = c->mesh.bc_fn[s];
+        for (int j = 0; j < 16; ++j) bc[s].p[j] = c->mesh.bc_params[s][j];
+    }
+    crk::set_bc_affine(bc, 1);
+    for (int s = 0; s < 4; ++s)
+        if (bc[s].type != crk::BC_PERIODIC && !bc[s].affine) return false;
+    return true;
+}
+
+// one wave of the modal step: as many warps as its registers and shared
+// memory let the 152 SMs hold, segments of >= 8 rows
+int linear_shape(crkdg_ctx* c) {
+    if (c->lin_seg_rows > 0) return CRKDG_OK;
+    crk::KernelInfo ki;
+    CK(crk::info_step2d_linear(c->precision, c->k, c->basis, c->tab.s, &ki));
+    const int wpb = std::max(1, std::min(4, ki.max_threads / 32));
+    const int regs_warp = ((ki.regs + 7) / 8) * 8 * 32;
+    const int by_regs = 65536 / regs_warp;
+    const int by_smem = (228 * 1024) / std::max(1, ki.smem_per_thread * 32);
+    int resident = std::min(64, std::min(by_regs, by_smem));
+    resident = std::max(wpb, resident / wpb * wpb);
+    const int ns = (c->mesh.nx + 29) / 30;
+    const long nseg = std::max(1L, 152L * resident / ns);
+    const int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
+    c->lin_seg_rows = std::min(L, c->mesh.ny);
+    c->lin_wpb = wpb;
+    return CRKDG_OK;
+}
+
 // the pending limit as an in-place pass over u[cur]; troubled cells are
 // counted into the run state, where the next step's epilogue reports them
 int enqueue_limit_pass(crkdg_ctx* c, double M, int dt_from_dev) {
@@ -229,7 +269,21 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
                 if (r) return r;
                 a.limit = 0;
             }
-            CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+            if (!a.limit && use_linear(c)) {
+                int r = linear_shape(c);
+                if (r) return r;
+                int lns, lnseg;
+                strips_segs(c, c->lin_seg_rows, &lns, &lnseg);
+                a.seg_len = c->lin_seg_rows;
+                a.n_strips = lns;
+                a.n_segs = lnseg;
+                r = ensure_partials(c, (size_t)lns * lnseg * 8);
+                if (r) return r;
+                a.partials = c->d_partials;
+                CK(crk::launch_step2d_linear(c->precision, c->k, c->basis, a, c->lin_wpb, c->stream));
+            } else {
+                CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));
+            }
         }
     } else {
         const int warps = (c->mesh.nx + 29) / 30;
@@ -522,6 +576,13 @@ int crkdg_advance(crkdg_ctx* c, int n_steps, double cfl, double t_end, int captu
     strips_segs(c, c->seg_rows, &ns, &nseg);
     r = ensure_partials(c, (size_t)ns * nseg * 8);
     if (r) return r;
+    if (use_linear(c)) {   // slots of the modal step too: nothing may allocate while a graph is captured
+        r = linear_shape(c);
+        if (r) return r;
+        strips_segs(c, c->lin_seg_rows, &ns, &nseg);
+        r = ensure_partials(c, (size_t)ns * nseg * 8);
+        if (r) return r;
+    }
     auto enqueue_all = [&]() -> int {
         for (int i = 0; i < n_steps; ++i) {
             const int lim = i == 0 ? lim_first : lim_rest;
@@ -842,6 +903,21 @@ int crkdg_set_limit_mode(crkdg_ctx* c, int mode) {
     c->limit_mode = mode;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    return CRKDG_OK;
+}
+
+int crkdg_set_operator_form(crkdg_ctx* c, int form) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (form != CRKDG_FORM_QUADRATURE && form != CRKDG_FORM_AUTO) return fail(CRKDG_EINVAL, "unknown operator form");
+    c->op_form = form;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return CRKDG_OK;
+}
+
+int crkdg_get_operator_form(const crkdg_ctx* c, int* form) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (form) *form = c->op_form;
     return CRKDG_OK;
 }
 

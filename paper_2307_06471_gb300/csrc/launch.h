@@ -52,6 +52,9 @@ cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, c
 cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,
                          cudaStream_t st);
 cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st);
+// the modal step for linear advection (step2d_linear.cuh); prec 0 FP32, 1 FP64
+cudaError_t launch_step2d_linear(int prec, int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t info_step2d_linear(int prec, int k, int basis, int s, KernelInfo* info);
 // FP64 staging <-> FP32 state of n elements: one plane set (comp = 0) or the
 // compensated hi + lo plane sets (comp = 1, lo at offset n)
 cudaError_t launch_f64_to_f32(const double* in, float* out, size_t n, int comp, cudaStream_t st);

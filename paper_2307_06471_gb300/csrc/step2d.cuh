@@ -147,6 +147,78 @@ struct ProbView {
     __device__ __forceinline__ bool copy_if_idle() const { return false; }
 };
 
+// FP64 epilogue of a step: warp reduction of the lane accumulators (max
+// wave speed, NV totals, troubled count, status bits) into the warp's slot,
+// then the last warp to arrive (atomic counter, no waiting) reduces all slots
+// in a fixed order and updates the device run state: t, the next dt =
+// min(cfl / max speed, t_end - t), totals, troubled count.
+template <int NV, int NRED, class PV>
+__device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, int gw, int lane, int total_warps,
+                                              double red_max, double* red_sum, unsigned red_trouble,
+                                              unsigned status, double cell, double t0, double dt) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red_sum[v] += __shfl_xor_sync(0xffffffffu, red_sum[v], off);
+        red_trouble += __shfl_xor_sync(0xffffffffu, red_trouble, off);
+        status |= __shfl_xor_sync(0xffffffffu, status, off);
+    }
+    double* slotp = pv.partials() + (size_t)gw * NRED;
+    unsigned prev = 0;
+    if (lane == 0) {
+        slotp[0] = red_max;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
+        slotp[1 + NV] = double(red_trouble);
+        if (status) atomicOr(&pv.ds()->status, status);
+        __threadfence();
+        prev = atomicAdd(&pv.ds()->counter, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned)total_warps - 1) return;
+    // last warp: fixed-order reduction of all per-warp slots (deterministic)
+    __threadfence();
+    double mx = 0.0, sm_[NV], tr = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
+    for (int wi = lane; wi < total_warps; wi += 32) {
+        const double* q = pv.partials() + (size_t)wi * NRED;
+        mx = fmax(mx, __ldcg(q));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
+        tr += __ldcg(q + 1 + NV);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
+        tr += __shfl_xor_sync(0xffffffffu, tr, off);
+    }
+    if (lane == 0) {
+        DevState* ds = pv.ds();
+        ds->maxspeed = mx;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
+        // troubled cells: this step's limit-on-load, else a separate pass over u^n
+        ds->troubled = a.limit ? tr : double(ds->lim_count);
+        ds->lim_count = 0;
+        const double tn = t0 + dt;
+        ds->t = tn;
+        double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
+        const double rem = ds->t_end - tn;
+        const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
+        if (dn > rem) dn = rem;
+        if (reached) dn = 0.0;
+        ds->dt = dn;
+        ds->steps += 1;
+        ds->counter = 0;
+        if (pv.cur()) *pv.cur() ^= 1;
+        if (pv.done() && reached) atomicAdd(pv.done(), 1u);
+    }
+}
+
 // COMP = true: compensated FP32 state.  The buffers hold hi planes followed
 // by lo planes (u = hi + lo); every stage computes in T from hi, and only the
 // final update u^{n+1} = u^n + Delta is accumulated exactly (TwoSum of hi and
@@ -833,67 +905,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
         for (int v = 0; v < NV; ++v) red_sum[v] = double(cs_hi[v]) + double(cs_lo[v]);
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
-#pragma unroll
-        for (int v = 0; v < NV; ++v) red_sum[v] += __shfl_xor_sync(0xffffffffu, red_sum[v], off);
-        red_trouble += __shfl_xor_sync(0xffffffffu, red_trouble, off);
-        status |= __shfl_xor_sync(0xffffffffu, status, off);
-    }
-    double* slotp = pv.partials() + (size_t)gw * C::NRED;
-    unsigned prev = 0;
-    if (lane == 0) {
-        slotp[0] = red_max;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
-        slotp[1 + NV] = double(red_trouble);
-        if (status) atomicOr(&pv.ds()->status, status);
-        __threadfence();
-        prev = atomicAdd(&pv.ds()->counter, 1u);
-    }
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != (unsigned)total_warps - 1) return;
-    // last warp: fixed-order reduction of all per-warp slots (deterministic)
-    __threadfence();
-    double mx = 0.0, sm_[NV], tr = 0.0;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
-    for (int wi = lane; wi < total_warps; wi += 32) {
-        const double* q = pv.partials() + (size_t)wi * C::NRED;
-        mx = fmax(mx, __ldcg(q));
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
-        tr += __ldcg(q + 1 + NV);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
-        tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    }
-    if (lane == 0) {
-        DevState* ds = pv.ds();
-        ds->maxspeed = mx;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
-        // troubled cells: this step's limit-on-load, else a separate pass over u^n
-        ds->troubled = a.limit ? tr : double(ds->lim_count);
-        ds->lim_count = 0;
-        const double tn = t0 + dt;
-        ds->t = tn;
-        double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
-        const double rem = ds->t_end - tn;
-        const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
-        if (dn > rem) dn = rem;
-        if (reached) dn = 0.0;
-        ds->dt = dn;
-        ds->steps += 1;
-        ds->counter = 0;
-        if (pv.cur()) *pv.cur() ^= 1;
-        if (pv.done() && reached) atomicAdd(pv.done(), 1u);
-    }
+    step_epilogue<NV, C::NRED>(a, pv, gw, lane, total_warps, red_max, red_sum, red_trouble, status, cell, t0, dt);
 }
 
 // One problem: the launch arguments describe the mesh; dt and t come from

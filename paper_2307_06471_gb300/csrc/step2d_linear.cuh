@@ -1,0 +1,269 @@
+// Fused cRKDG time step for the linear flux f(u) = (bx u, by u) in modal form.
+//
+// With a linear flux and the Lax--Friedrichs flux of speed alpha = |beta . n|
+// (the upwind flux), both operators of the cRKDG step (eq. (2.8)) are fixed
+// linear maps of the modal coefficients, and the quadrature forms of
+// step2d.cuh evaluate them exactly:
+//   - the local operator (eq. (2.7)) of a P^k / Q^k state w is beta . grad w
+//     itself (its derivative stays in the space), i.e.
+//     L_loc(w) = (2 bx / dx) d/dxi w + (2 by / dy) d/deta w with the Legendre
+//     derivative d/dxi P_i = sum_{i' = i-1, i-3, ...} (2i'+1) P_i';
+//   - the DG operator (eq. (2.3)) is the local operator plus, on each inflow
+//     face (beta . n < 0), (beta . n)(w_ext - w_int) lifted to the modes:
+//     (2i+1) P_i(+-1) / dx per trace coefficient on the E/W faces,
+//     (2j+1) P_j(+-1) / dy on the N/S faces; the trace coefficients are
+//     sums of the modes with P_i(+-1) = (+-1)^i;
+//   - being linear, the final stage sum_i b_i L_DG(u^(i)) equals
+//     L_DG(sum_i b_i u^(i)) (the identity behind Theorem 3.3), so the face
+//     coupling is needed once per step, for wbar = sum_i b_i u^(i).
+// The work decomposition is step2d.cuh's (marching warps, 30 columns + 2 halo
+// lanes, segments of rows, the row below finished when the current row's
+// south trace is known) with a tenth of its arithmetic, so the step is bound
+// by HBM.  Boundary sides: periodic, or an exterior state affine in the
+// interior one (outflow, wall, constant state; BCSide::affine).
+#pragma once
+#include "step2d.cuh"
+
+namespace crk {
+
+template <int K, int B>
+struct LinTab {
+    static constexpr int NM = n_modes_2d(K, B);
+    double dxi[NM][NM];    // d/dxi phi_c = sum_r dxi[r][c] phi_r
+    double deta[NM][NM];   // d/deta phi_c = sum_r deta[r][c] phi_r
+    int mi[NM], mj[NM];    // Legendre degrees of mode m in xi and eta
+    double li[NM], lj[NM]; // 2i+1, 2j+1
+    double si[NM], sj[NM]; // P_i(-1), P_j(-1)
+};
+
+template <int K, int B>
+constexpr LinTab<K, B> make_lintab() {
+    LinTab<K, B> t{};
+    constexpr int NM = LinTab<K, B>::NM;
+    for (int m = 0; m < NM; ++m) {
+        int i = 0, j = 0;
+        mode_ij(K, B, m, i, j);
+        t.mi[m] = i;
+        t.mj[m] = j;
+        t.li[m] = 2.0 * i + 1.0;
+        t.lj[m] = 2.0 * j + 1.0;
+        t.si[m] = (i % 2) ? -1.0 : 1.0;
+        t.sj[m] = (j % 2) ? -1.0 : 1.0;
+    }
+    for (int r = 0; r < NM; ++r)
+        for (int c = 0; c < NM; ++c) {
+            const int ir = t.mi[r], jr = t.mj[r], ic = t.mi[c], jc = t.mj[c];
+            t.dxi[r][c] = (jc == jr && ic > ir && (ic - ir) % 2 == 1) ? 2.0 * ir + 1.0 : 0.0;
+            t.deta[r][c] = (ic == ir && jc > jr && (jc - jr) % 2 == 1) ? 2.0 * jr + 1.0 : 0.0;
+        }
+    return t;
+}
+
+// private shared memory per thread: the local operator of stages 1 .. s-1
+template <class T, int K, int B>
+__host__ __device__ constexpr int linear_smem_per_thread(int s) {
+    return (s > 1 ? s - 1 : 1) * n_modes_2d(K, B);
+}
+
+template <class T, int K, int B>
+__global__ void __launch_bounds__(256) step2d_linear_kernel(const StepArgs a) {
+    constexpr LinTab<K, B> lt = make_lintab<K, B>();
+    constexpr int NM = LinTab<K, B>::NM;
+    constexpr int NT = K + 1;   // trace coefficients per face
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
+
+    const int gw = blockIdx.x * (nthr >> 5) + (tid >> 5);
+    const int total_warps = a.n_strips * a.n_segs;
+    if (gw >= total_warps) return;   // whole warp leaves; no block barriers
+    const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};
+
+    const int nx = a.nx, ny = a.ny;
+    const size_t plane = (size_t)nx * ny;
+    const T* __restrict__ uin = static_cast<const T*>(a.uin);
+    T* __restrict__ uout = static_cast<T*>(a.uout);
+    const double dt = pv.dt();
+    const double t0 = pv.t();
+
+    const int strip = gw % a.n_strips;
+    const int seg = gw / a.n_strips;
+    const int xs = strip * 30;
+    const int col = xs - 1 + lane;
+    const bool perx = a.bc[0].type == BC_PERIODIC;
+    const bool pery = a.bc[2].type == BC_PERIODIC;
+    int xl = ((col % nx) + nx) % nx;
+    if (!perx) xl = col < 0 ? 0 : (col >= nx ? nx - 1 : col);
+    const bool outlane = lane >= 1 && lane <= 30 && col < nx;
+    const int r0 = (int)(((long long)seg * ny) / a.n_segs);
+    const int r1 = (int)(((long long)(seg + 1) * ny) / a.n_segs);
+    const int rstart = (r0 > 0 || pery) ? r0 - 1 : r0;
+    const int rend = (r1 < ny || pery) ? r1 : r1 - 1;
+
+    if (!(dt > 0.0)) {   // a non-positive dt leaves the state unchanged
+        if (outlane)
+            for (int r = r0; r < r1; ++r)
+                for (int m = 0; m < NM; ++m) uout[m * plane + (size_t)r * nx + col] = uin[m * plane + (size_t)r * nx + col];
+        return;
+    }
+
+    const T tdt = T(dt);
+    const T cx = T(2.0 * a.beta[0] / a.dx), cy = T(2.0 * a.beta[1] / a.dy);
+    // lifts of the inflow-face jumps: W (bx > 0), E (bx < 0), S (by > 0), N (by < 0)
+    const bool inW = a.beta[0] > 0.0, inE = a.beta[0] < 0.0, inS = a.beta[1] > 0.0, inN = a.beta[1] < 0.0;
+    const T kW = T(-a.beta[0] / a.dx), kE = T(a.beta[0] / a.dx), kS = T(-a.beta[1] / a.dy), kN = T(a.beta[1] / a.dy);
+    const int S = a.s;
+    // exterior trace at a non-periodic side: m * interior + constant state
+    auto bc_trace = [&](int side, const T* in, T* out) {
+        const BCSide& b = a.bc[side];
+        const T c = sizeof(T) == 4 ? T(b.cf[0]) : T(b.cd[0]);
+#pragma unroll
+        for (int q = 0; q < NT; ++q) out[q] = T(b.m[0]) * in[q] + (q == 0 ? c : T(0));
+    };
+
+    T cs_hi = T(0), cs_lo = T(0);   // compensated column total
+    unsigned status = 0;
+    T prevN[NT];                    // north trace of wbar, row below
+    T P[NM];                        // row below: u^{n+1} without its north-face term
+#pragma unroll
+    for (int q = 0; q < NT; ++q) prevN[q] = T(0);
+#pragma unroll
+    for (int m = 0; m < NM; ++m) P[m] = T(0);
+
+    auto write_row = [&](int rw) {
+        if (!outlane) return;
+        const size_t o = (size_t)rw * nx + col;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) uout[m * plane + o] = P[m];
+        const T sum = cs_hi + P[0];   // TwoSum
+        const T bv = sum - cs_hi;
+        cs_lo += (cs_hi - (sum - bv)) + (P[0] - bv);
+        cs_hi = sum;
+        if (!(P[0] == P[0])) status |= ST_NAN;
+    };
+
+    for (int r = rstart; r <= rend; ++r) {
+        const int ry_ = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const bool out_row = r >= r0 && r < r1;
+        const bool south_bc = (r == 0) && !pery;
+        const size_t cidx = (size_t)ry_ * nx + xl;
+        T un[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) un[m] = uin[m * plane + cidx];
+
+        // stages (eq. (2.8), first line) and wbar = sum_i b_i u^(i)
+        T wbar[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) wbar[m] = T(0);
+        for (int i = 0; i < S; ++i) {
+            T w[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) w[m] = un[m];
+            for (int j = 0; j < i; ++j) {
+                const T aij = tab_aT<T>(a, i, j);
+                if (aij == T(0)) continue;
+                const T c = aij * tdt;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) w[m] -= c * slot(j * NM + m);
+            }
+            if (i < S - 1) {
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    T d = T(0);
+#pragma unroll
+                    for (int c = 0; c < NM; ++c) {
+                        if (lt.dxi[m][c] != 0.0) d += (cx * T(lt.dxi[m][c])) * w[c];
+                        if (lt.deta[m][c] != 0.0) d += (cy * T(lt.deta[m][c])) * w[c];
+                    }
+                    slot(i * NM + m) = d;
+                }
+            }
+            const T bi = tab_bT<T>(a, i);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) wbar[m] += bi * w[m];
+        }
+
+        // DG operator of wbar: local part, then the inflow-face jumps
+        T Lw[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            T d = T(0);
+#pragma unroll
+            for (int c = 0; c < NM; ++c) {
+                if (lt.dxi[m][c] != 0.0) d += (cx * T(lt.dxi[m][c])) * wbar[c];
+                if (lt.deta[m][c] != 0.0) d += (cy * T(lt.deta[m][c])) * wbar[c];
+            }
+            Lw[m] = d;
+        }
+        T tE[NT], tW[NT], tN[NT], tS[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) tE[q] = tW[q] = tN[q] = tS[q] = T(0);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            tE[lt.mj[m]] += wbar[m];
+            tW[lt.mj[m]] += T(lt.si[m]) * wbar[m];
+            tN[lt.mi[m]] += wbar[m];
+            tS[lt.mi[m]] += T(lt.sj[m]) * wbar[m];
+        }
+        T extW[NT], extE[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            extW[q] = shfl_up(tE[q], 1);     // west neighbour's east trace
+            extE[q] = shfl_down(tW[q], 1);   // east neighbour's west trace
+        }
+        if (!perx && col == 0) bc_trace(0, tW, extW);
+        if (!perx && col == nx - 1) bc_trace(1, tE, extE);
+        if (inW) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Lw[m] += (kW * T(lt.li[m] * lt.si[m])) * (extW[lt.mj[m]] - tW[lt.mj[m]]);
+        }
+        if (inE) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Lw[m] += (kE * T(lt.li[m])) * (extE[lt.mj[m]] - tE[lt.mj[m]]);
+        }
+        if (inS && (r > rstart || south_bc)) {
+            T extS[NT];
+            if (south_bc) {
+                bc_trace(2, tS, extS);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NT; ++q) extS[q] = prevN[q];
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Lw[m] += (kS * T(lt.lj[m] * lt.sj[m])) * (extS[lt.mi[m]] - tS[lt.mi[m]]);
+        }
+
+        // the row below: its north face is this row's south face
+        if (r > rstart && r - 1 >= r0 && r - 1 < r1) {
+            if (inN) {
+#pragma unroll
+                for (int m = 0; m < NM; ++m) P[m] -= tdt * ((kN * T(lt.lj[m])) * (tS[lt.mi[m]] - prevN[lt.mi[m]]));
+            }
+            write_row(r - 1);
+        }
+        if (out_row) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) P[m] = un[m] - tdt * Lw[m];
+            if (r == ny - 1 && !pery) {   // top boundary: north face from the boundary state
+                if (inN) {
+                    T extN[NT];
+                    bc_trace(3, tN, extN);
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) P[m] -= tdt * ((kN * T(lt.lj[m])) * (extN[lt.mi[m]] - tN[lt.mi[m]]));
+                }
+                write_row(r);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NT; ++q) prevN[q] = tN[q];
+    }
+
+    double red_max = (outlane && r0 < r1) ? fabs(a.beta[0]) / a.dx + fabs(a.beta[1]) / a.dy : 0.0;
+    double red_sum[1] = {double(cs_hi) + double(cs_lo)};
+    step_epilogue<1, 3>(a, pv, gw, lane, total_warps, red_max, red_sum, 0u, status, a.dx * a.dy, t0, dt);
+}
+
+}  // namespace crk

@@ -101,15 +101,18 @@ def test_advection_with_inflow_boundaries_f64(k, basis):
     assert rel_err(from_planes(gs.get_state()), w) < 1e-12
 
 
+@pytest.mark.parametrize("form", ["quadrature", "modal"])
 @pytest.mark.parametrize("k,basis,launch", [(0, "P", None), (1, "P", (9, 2)), (2, "Q", None), (2, "P", (9, 4)),
                                             (3, "Q", None)])
-def test_advection_f32_matches_oracle(k, basis, launch):
-    """The FP32 scalar step (compiled for two blocks per SM) against the
-    FP64 oracle: periodic linear advection, five SSP-RK3 steps, on a mesh of
-    ragged strips and segments, with the residency-based default launch shape
-    or a fixed one."""
+def test_advection_f32_matches_oracle(k, basis, launch, form):
+    """The FP32 scalar step against the FP64 oracle: periodic linear
+    advection, five SSP-RK3 steps, on a mesh of ragged strips and segments;
+    the quadrature form (compiled for two blocks per SM; residency-based
+    default launch shape or a fixed one) and the modal form."""
+    from paper_2307_06471_gb300 import binding as B
     nx, ny = 301, 203
     gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 1), k, basis, "advection", "ssprk3", PER, "f32", beta=(1.0, 0.5))
+    gs.set_operator_form(B.FORM_QUADRATURE if form == "quadrature" else B.FORM_AUTO)
     if launch:
         gs.set_launch(*launch)
     u = inp.random_modal_state(ny, nx, k, basis, "advection", seed=21)
@@ -122,6 +125,35 @@ def test_advection_f32_matches_oracle(k, basis, launch):
         w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3)
         t += dt
     assert rel_err(from_planes(gs.get_state()), w) < 1e-5
+
+
+@pytest.mark.parametrize("beta", [(1.0, 0.5), (-1.0, 0.5), (0.7, -1.2), (-0.4, -0.9), (0.0, 1.0)])
+@pytest.mark.parametrize("k,basis", [(1, "P"), (2, "Q"), (3, "P"), (2, "P")])
+def test_modal_advection_f64_matches_oracle(k, basis, beta):
+    """The modal form of the step (linear flux: exact derivative operators,
+    the final stage's DG operator applied once to sum_i b_i u^(i)) against
+    the FP64 oracle's quadrature form to 1e-12: every inflow direction,
+    outflow and constant-state sides, four SSP-RK3 steps; and the modal and
+    quadrature forms of the GPU step agree with each other."""
+    from paper_2307_06471_gb300 import binding as B
+    bcs = {"W": ("const", [0.3]), "E": ("outflow",), "S": ("outflow",), "N": ("const", [-0.2])}
+    nx, ny = 97, 45
+    u = inp.random_modal_state(ny, nx, k, basis, "advection", seed=31)
+    res = {}
+    for form in (B.FORM_AUTO, B.FORM_QUADRATURE):
+        gs, dg = make_pair_2d(nx, ny, (0, 1, 0, 0.5), k, basis, "advection", "ssprk3", bcs, "f64", beta=beta)
+        gs.set_operator_form(form)
+        gs.set_state(to_planes(u), 0.0)
+        dt = 0.15 / (abs(beta[0]) * nx + abs(beta[1]) * ny / 0.5)
+        w, t = u.copy(), 0.0
+        for _ in range(4):
+            gs.step(dt)
+            w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3)
+            t += dt
+        res[form] = from_planes(gs.get_state())
+        assert rel_err(res[form], w) < 1e-12
+        assert gs.sync() == (0, 0)
+    assert rel_err(res[B.FORM_AUTO], res[B.FORM_QUADRATURE]) < 1e-13
 
 
 def _dmr_bcs():
