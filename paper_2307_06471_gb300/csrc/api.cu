@@ -280,6 +280,22 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
                 r = ensure_partials(c, (size_t)lns * lnseg * 8);
                 if (r) return r;
                 a.partials = c->d_partials;
+                // gamma_l = b^T A^l 1 of the tableau (FP64, host)
+                const int s = c->tab.s;
+                double v[crk::MAXS];
+                for (int i = 0; i < s; ++i) v[i] = 1.0;
+                for (int l = 0; l < crk::MAXS; ++l) {
+                    double g = 0.0;
+                    if (l < s)
+                        for (int i = 0; i < s; ++i) g += c->tab.b[i] * v[i];
+                    a.lin_gamma[l] = g;
+                    double nv[crk::MAXS];
+                    for (int i = 0; i < s; ++i) {
+                        nv[i] = 0.0;
+                        for (int j = 0; j < s; ++j) nv[i] += c->tab.a[i * CRKDG_MAX_STAGES + j] * v[j];
+                    }
+                    for (int i = 0; i < s; ++i) v[i] = nv[i];
+                }
                 CK(crk::launch_step2d_linear(c->precision, c->k, c->basis, a, c->lin_wpb, c->stream));
             } else {
                 CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));

@@ -60,6 +60,9 @@ struct StepArgs {
     double pp_eps;            // > 0: positivity-preserving scaling with this floor
     double gamma;
     double beta[2];
+    // sum_i b_i u^(i) = sum_l lin_gamma[l] (-dt D)^l u^n for a linear local
+    // operator D: lin_gamma[l] = b^T A^l 1 (the modal linear step)
+    double lin_gamma[MAXS];
     // limiter parameters as the one-thread-per-cell limiter pass takes them
     // (filled by set_limiter_params at its launch)
     float Mdx2f, Mdy2f, gammaf, pp_epsf;

@@ -24,6 +24,11 @@
 #pragma once
 #include "step2d.cuh"
 
+// blocks of 256 threads per SM the modal step is compiled for (tuning knob)
+#ifndef CRK_LIN_MINB
+#define CRK_LIN_MINB 2
+#endif
+
 namespace crk {
 
 template <int K, int B>
@@ -59,23 +64,20 @@ constexpr LinTab<K, B> make_lintab() {
     return t;
 }
 
-// private shared memory per thread: the local operator of stages 1 .. s-1
+// private shared memory per thread (none: the stages are combined in registers)
 template <class T, int K, int B>
-__host__ __device__ constexpr int linear_smem_per_thread(int s) {
-    return (s > 1 ? s - 1 : 1) * n_modes_2d(K, B);
+__host__ __device__ constexpr int linear_smem_per_thread(int) {
+    return 0;
 }
 
 template <class T, int K, int B>
-__global__ void __launch_bounds__(256) step2d_linear_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const StepArgs a) {
     constexpr LinTab<K, B> lt = make_lintab<K, B>();
     constexpr int NM = LinTab<K, B>::NM;
     constexpr int NT = K + 1;   // trace coefficients per face
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
 
     const int gw = blockIdx.x * (nthr >> 5) + (tid >> 5);
     const int total_warps = a.n_strips * a.n_segs;
@@ -116,6 +118,9 @@ __global__ void __launch_bounds__(256) step2d_linear_kernel(const StepArgs a) {
     const bool inW = a.beta[0] > 0.0, inE = a.beta[0] < 0.0, inS = a.beta[1] > 0.0, inN = a.beta[1] < 0.0;
     const T kW = T(-a.beta[0] / a.dx), kE = T(a.beta[0] / a.dx), kS = T(-a.beta[1] / a.dy), kN = T(a.beta[1] / a.dy);
     const int S = a.s;
+    T gam[MAXS];
+#pragma unroll
+    for (int l = 0; l < MAXS; ++l) gam[l] = T(a.lin_gamma[l]);
     // exterior trace at a non-periodic side: m * interior + constant state
     auto bc_trace = [&](int side, const T* in, T* out) {
         const BCSide& b = a.bc[side];
@@ -145,45 +150,51 @@ __global__ void __launch_bounds__(256) step2d_linear_kernel(const StepArgs a) {
         if (!(P[0] == P[0])) status |= ST_NAN;
     };
 
+    // u^n of the next row is loaded while the current row computes
+    auto row_index = [&](int r) -> size_t {
+        const int ry = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        return (size_t)ry * nx + xl;
+    };
+    T unext[NM];
+    {
+        const size_t c0 = row_index(rstart);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) unext[m] = uin[m * plane + c0];
+    }
     for (int r = rstart; r <= rend; ++r) {
-        const int ry_ = r < 0 ? r + ny : (r >= ny ? r - ny : r);
         const bool out_row = r >= r0 && r < r1;
         const bool south_bc = (r == 0) && !pery;
-        const size_t cidx = (size_t)ry_ * nx + xl;
         T un[NM];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) un[m] = uin[m * plane + cidx];
+        for (int m = 0; m < NM; ++m) un[m] = unext[m];
+        if (r < rend) {
+            const size_t cn = row_index(r + 1);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) unext[m] = uin[m * plane + cn];
+        }
 
-        // stages (eq. (2.8), first line) and wbar = sum_i b_i u^(i)
+        // stages (eq. (2.8), first line) combined: with the local operator the
+        // fixed linear map D, u^(i) = sum_l (A^l 1)_i (-dt D)^l u^n, hence
+        // wbar = sum_i b_i u^(i) = sum_l gamma_l (-dt D)^l u^n, gamma_l =
+        // b^T A^l 1 (Horner: s - 1 applications of D)
         T wbar[NM];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) wbar[m] = T(0);
-        for (int i = 0; i < S; ++i) {
-            T w[NM];
+        for (int m = 0; m < NM; ++m) wbar[m] = T(gam[S - 1]) * un[m];
+        for (int l = S - 2; l >= 0; --l) {
+            T d[NM];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) w[m] = un[m];
-            for (int j = 0; j < i; ++j) {
-                const T aij = tab_aT<T>(a, i, j);
-                if (aij == T(0)) continue;
-                const T c = aij * tdt;
+            for (int m = 0; m < NM; ++m) {
+                T acc = T(0);
 #pragma unroll
-                for (int m = 0; m < NM; ++m) w[m] -= c * slot(j * NM + m);
-            }
-            if (i < S - 1) {
-#pragma unroll
-                for (int m = 0; m < NM; ++m) {
-                    T d = T(0);
-#pragma unroll
-                    for (int c = 0; c < NM; ++c) {
-                        if (lt.dxi[m][c] != 0.0) d += (cx * T(lt.dxi[m][c])) * w[c];
-                        if (lt.deta[m][c] != 0.0) d += (cy * T(lt.deta[m][c])) * w[c];
-                    }
-                    slot(i * NM + m) = d;
+                for (int c = 0; c < NM; ++c) {
+                    if (lt.dxi[m][c] != 0.0) acc += (cx * T(lt.dxi[m][c])) * wbar[c];
+                    if (lt.deta[m][c] != 0.0) acc += (cy * T(lt.deta[m][c])) * wbar[c];
                 }
+                d[m] = acc;
             }
-            const T bi = tab_bT<T>(a, i);
+            const T gl = gam[l];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) wbar[m] += bi * w[m];
+            for (int m = 0; m < NM; ++m) wbar[m] = gl * un[m] - tdt * d[m];
         }
 
         // DG operator of wbar: local part, then the inflow-face jumps
