@@ -289,6 +289,7 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
                     if (l < s)
                         for (int i = 0; i < s; ++i) g += c->tab.b[i] * v[i];
                     a.lin_gamma[l] = g;
+                    a.lin_gammaf[l] = (float)g;
                     double nv[crk::MAXS];
                     for (int i = 0; i < s; ++i) {
                         nv[i] = 0.0;
@@ -296,6 +297,8 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
                     }
                     for (int i = 0; i < s; ++i) v[i] = nv[i];
                 }
+                a.lin_inflow = (a.beta[0] > 0.0 ? 1 : 0) | (a.beta[0] < 0.0 ? 2 : 0) | (a.beta[1] > 0.0 ? 4 : 0) |
+                               (a.beta[1] < 0.0 ? 8 : 0);
                 CK(crk::launch_step2d_linear(c->precision, c->k, c->basis, a, c->lin_wpb, c->stream));
             } else {
                 CK(crk::launch_step2d(c->kphys, c->precision, c->k, c->basis, a, c->wpb, c->stream));

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "tables.cuh"
 
 namespace crk {
@@ -63,6 +66,8 @@ struct StepArgs {
     // sum_i b_i u^(i) = sum_l lin_gamma[l] (-dt D)^l u^n for a linear local
     // operator D: lin_gamma[l] = b^T A^l 1 (the modal linear step)
     double lin_gamma[MAXS];
+    float lin_gammaf[MAXS];
+    int lin_inflow;           // inflow faces of every cell: bit 0 W, 1 E, 2 S, 3 N (the modal linear step)
     // limiter parameters as the one-thread-per-cell limiter pass takes them
     // (filled by set_limiter_params at its launch)
     float Mdx2f, Mdy2f, gammaf, pp_epsf;
@@ -274,6 +279,22 @@ template <class T>
 __device__ __forceinline__ T tab_bT(const StepArgs& a, int i) {
     if constexpr (sizeof(T) == 4) return __ldg(reinterpret_cast<const float*>(a.tab + TAB_F64) + MAXS * MAXS + i);
     else return tab_b(a, i);
+}
+
+// Entry of a rarely taken branch (boundary data): no memory access, and so no
+// arithmetic on launch parameters, is hoisted above it into the common path,
+// where it would run (predicated or speculated) on every row.
+__device__ __forceinline__ void cold_branch() { asm volatile("" ::: "memory"); }
+
+// f(std::integral_constant<int, i>) for i = 0 .. N-1: loops whose index must
+// be a constant expression (table entries folded at compile time)
+template <class F, int... I>
+__device__ __forceinline__ void static_for_seq(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_seq(f, std::make_integer_sequence<int, N>{});
 }
 
 template <class T>

@@ -670,6 +670,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                                 tE[p][v] = edge ? ext : tE[p][v];
                             }
                     } else {
+                        cold_branch();
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
@@ -695,6 +696,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                                 tWn[p][v] = edge ? ext : tWn[p][v];
                             }
                     } else {
+                        cold_branch();
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
@@ -718,21 +720,26 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             }
             // south face: north trace of the row below (stored) vs. own south trace
             if (do_south && !fuseS) {
+                T lo[NQ][NV];
+                if (south_bc) {   // row 0 without periodic wrap: boundary data (one uniform branch per row)
+                    cold_branch();
 #pragma unroll
-                for (int p = 0; p < NQ; ++p) {
-                    T lo[NV];
-                    if (south_bc) {
+                    for (int p = 0; p < NQ; ++p)
                         bc_exterior<T, NV>(a.bc[2], 1, tS[p], [&](double& x, double& y, double& t) {
                             x = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
                             y = pv.y0();
                             t = ti();
-                        }, lo);
-                    } else {
+                        }, lo[p]);
+                } else {
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
-                    }
+                    for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) lo[p][v] = slot(offN + (i * NQ + p) * NV + v);
+                }
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) {
                     T F[NV];
-                    llf<T, PHYS, 1>(ph, lo, tS[p], F);
+                    llf<T, PHYS, 1>(ph, lo[p], tS[p], F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FS[p][v] += bi * F[v];
                 }
@@ -856,6 +863,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             }
         if (r == ny - 1 && !pery) {
             // top boundary: north face flux from the stored north traces
+            cold_branch();
             T FN[NQ][NV];
 #pragma unroll
             for (int p = 0; p < NQ; ++p)

@@ -24,44 +24,37 @@
 #pragma once
 #include "step2d.cuh"
 
-// blocks of 256 threads per SM the modal step is compiled for (tuning knob)
+// blocks of 256 threads per SM the FP32 modal step is compiled for (tuning knob)
 #ifndef CRK_LIN_MINB
 #define CRK_LIN_MINB 2
 #endif
 
 namespace crk {
 
+// Degrees of mode m and the entries of the Legendre derivative matrices,
+// as constexpr functions (called with constant-expression arguments only)
 template <int K, int B>
-struct LinTab {
-    static constexpr int NM = n_modes_2d(K, B);
-    double dxi[NM][NM];    // d/dxi phi_c = sum_r dxi[r][c] phi_r
-    double deta[NM][NM];   // d/deta phi_c = sum_r deta[r][c] phi_r
-    int mi[NM], mj[NM];    // Legendre degrees of mode m in xi and eta
-    double li[NM], lj[NM]; // 2i+1, 2j+1
-    double si[NM], sj[NM]; // P_i(-1), P_j(-1)
-};
-
+constexpr int lin_mi(int m) {
+    int i = 0, j = 0;
+    mode_ij(K, B, m, i, j);
+    return i;
+}
 template <int K, int B>
-constexpr LinTab<K, B> make_lintab() {
-    LinTab<K, B> t{};
-    constexpr int NM = LinTab<K, B>::NM;
-    for (int m = 0; m < NM; ++m) {
-        int i = 0, j = 0;
-        mode_ij(K, B, m, i, j);
-        t.mi[m] = i;
-        t.mj[m] = j;
-        t.li[m] = 2.0 * i + 1.0;
-        t.lj[m] = 2.0 * j + 1.0;
-        t.si[m] = (i % 2) ? -1.0 : 1.0;
-        t.sj[m] = (j % 2) ? -1.0 : 1.0;
-    }
-    for (int r = 0; r < NM; ++r)
-        for (int c = 0; c < NM; ++c) {
-            const int ir = t.mi[r], jr = t.mj[r], ic = t.mi[c], jc = t.mj[c];
-            t.dxi[r][c] = (jc == jr && ic > ir && (ic - ir) % 2 == 1) ? 2.0 * ir + 1.0 : 0.0;
-            t.deta[r][c] = (ic == ir && jc > jr && (jc - jr) % 2 == 1) ? 2.0 * jr + 1.0 : 0.0;
-        }
-    return t;
+constexpr int lin_mj(int m) {
+    int i = 0, j = 0;
+    mode_ij(K, B, m, i, j);
+    return j;
+}
+// d/dxi phi_c = sum_r lin_dxi(r, c) phi_r, d/deta likewise
+template <int K, int B>
+constexpr double lin_dxi(int r, int c) {
+    const int ir = lin_mi<K, B>(r), jr = lin_mj<K, B>(r), ic = lin_mi<K, B>(c), jc = lin_mj<K, B>(c);
+    return (jc == jr && ic > ir && (ic - ir) % 2 == 1) ? 2.0 * ir + 1.0 : 0.0;
+}
+template <int K, int B>
+constexpr double lin_deta(int r, int c) {
+    const int ir = lin_mi<K, B>(r), jr = lin_mj<K, B>(r), ic = lin_mi<K, B>(c), jc = lin_mj<K, B>(c);
+    return (ic == ir && jc > jr && (jc - jr) % 2 == 1) ? 2.0 * jr + 1.0 : 0.0;
 }
 
 // private shared memory per thread (none: the stages are combined in registers)
@@ -71,9 +64,8 @@ __host__ __device__ constexpr int linear_smem_per_thread(int) {
 }
 
 template <class T, int K, int B>
-__global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const StepArgs a) {
-    constexpr LinTab<K, B> lt = make_lintab<K, B>();
-    constexpr int NM = LinTab<K, B>::NM;
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? CRK_LIN_MINB : 1) step2d_linear_kernel(const StepArgs a) {
+    constexpr int NM = n_modes_2d(K, B);
     constexpr int NT = K + 1;   // trace coefficients per face
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
@@ -115,12 +107,26 @@ __global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const 
     const T tdt = T(dt);
     const T cx = T(2.0 * a.beta[0] / a.dx), cy = T(2.0 * a.beta[1] / a.dy);
     // lifts of the inflow-face jumps: W (bx > 0), E (bx < 0), S (by > 0), N (by < 0)
-    const bool inW = a.beta[0] > 0.0, inE = a.beta[0] < 0.0, inS = a.beta[1] > 0.0, inN = a.beta[1] < 0.0;
+    // integer flags (set on the host): tests on the FP64 launch parameters
+    // would be re-evaluated on GB300's narrow FP64 pipe at every use
+    const int inflow = a.lin_inflow;
+    const bool inW = inflow & 1, inE = inflow & 2, inS = inflow & 4, inN = inflow & 8;
     const T kW = T(-a.beta[0] / a.dx), kE = T(a.beta[0] / a.dx), kS = T(-a.beta[1] / a.dy), kN = T(a.beta[1] / a.dy);
     const int S = a.s;
-    T gam[MAXS];
-#pragma unroll
-    for (int l = 0; l < MAXS; ++l) gam[l] = T(a.lin_gamma[l]);
+    // out = D w: the local operator (2 bx / dx) d/dxi + (2 by / dy) d/deta
+    auto applyD = [&](const T* w, T* out) {
+        static_for<NM>([&](auto mr) {
+            constexpr int m = decltype(mr)::value;
+            T acc = T(0);
+            static_for<NM>([&](auto cc) {
+                constexpr int c = decltype(cc)::value;
+                constexpr double ex = lin_dxi<K, B>(m, c), ey = lin_deta<K, B>(m, c);
+                if constexpr (ex != 0.0) acc += (cx * T(ex)) * w[c];
+                if constexpr (ey != 0.0) acc += (cy * T(ey)) * w[c];
+            });
+            out[m] = acc;
+        });
+    };
     // exterior trace at a non-periodic side: m * interior + constant state
     auto bc_trace = [&](int side, const T* in, T* out) {
         const BCSide& b = a.bc[side];
@@ -178,47 +184,40 @@ __global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const 
         // wbar = sum_i b_i u^(i) = sum_l gamma_l (-dt D)^l u^n, gamma_l =
         // b^T A^l 1 (Horner: s - 1 applications of D)
         T wbar[NM];
+        bool started = false;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) wbar[m] = T(gam[S - 1]) * un[m];
-        for (int l = S - 2; l >= 0; --l) {
-            T d[NM];
+        for (int l = MAXS - 1; l >= 0; --l) {
+            if (l < S) {
+                const T gl = sizeof(T) == 4 ? T(a.lin_gammaf[l]) : T(a.lin_gamma[l]);
+                if (started) {
+                    T d[NM];
+                    applyD(wbar, d);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                T acc = T(0);
+                    for (int m = 0; m < NM; ++m) wbar[m] = gl * un[m] - tdt * d[m];
+                } else {
 #pragma unroll
-                for (int c = 0; c < NM; ++c) {
-                    if (lt.dxi[m][c] != 0.0) acc += (cx * T(lt.dxi[m][c])) * wbar[c];
-                    if (lt.deta[m][c] != 0.0) acc += (cy * T(lt.deta[m][c])) * wbar[c];
+                    for (int m = 0; m < NM; ++m) wbar[m] = gl * un[m];
+                    started = true;
                 }
-                d[m] = acc;
             }
-            const T gl = gam[l];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) wbar[m] = gl * un[m] - tdt * d[m];
         }
 
         // DG operator of wbar: local part, then the inflow-face jumps
         T Lw[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            T d = T(0);
-#pragma unroll
-            for (int c = 0; c < NM; ++c) {
-                if (lt.dxi[m][c] != 0.0) d += (cx * T(lt.dxi[m][c])) * wbar[c];
-                if (lt.deta[m][c] != 0.0) d += (cy * T(lt.deta[m][c])) * wbar[c];
-            }
-            Lw[m] = d;
-        }
+        applyD(wbar, Lw);
         T tE[NT], tW[NT], tN[NT], tS[NT];
 #pragma unroll
         for (int q = 0; q < NT; ++q) tE[q] = tW[q] = tN[q] = tS[q] = T(0);
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            tE[lt.mj[m]] += wbar[m];
-            tW[lt.mj[m]] += T(lt.si[m]) * wbar[m];
-            tN[lt.mi[m]] += wbar[m];
-            tS[lt.mi[m]] += T(lt.sj[m]) * wbar[m];
-        }
+        static_for<NM>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
+            constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+            tE[j] += wbar[m];
+            tN[i] += wbar[m];
+            if constexpr (i % 2) tW[j] -= wbar[m];
+            else tW[j] += wbar[m];
+            if constexpr (j % 2) tS[i] -= wbar[m];
+            else tS[i] += wbar[m];
+        });
         T extW[NT], extE[NT];
 #pragma unroll
         for (int q = 0; q < NT; ++q) {
@@ -228,12 +227,19 @@ __global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const 
         if (!perx && col == 0) bc_trace(0, tW, extW);
         if (!perx && col == nx - 1) bc_trace(1, tE, extE);
         if (inW) {
-#pragma unroll
-            for (int m = 0; m < NM; ++m) Lw[m] += (kW * T(lt.li[m] * lt.si[m])) * (extW[lt.mj[m]] - tW[lt.mj[m]]);
+            static_for<NM>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+                constexpr double f = (2.0 * i + 1.0) * ((i % 2) ? -1.0 : 1.0);
+                Lw[m] += (kW * T(f)) * (extW[j] - tW[j]);
+            });
         }
         if (inE) {
-#pragma unroll
-            for (int m = 0; m < NM; ++m) Lw[m] += (kE * T(lt.li[m])) * (extE[lt.mj[m]] - tE[lt.mj[m]]);
+            static_for<NM>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+                Lw[m] += (kE * T(2.0 * i + 1.0)) * (extE[j] - tE[j]);
+            });
         }
         if (inS && (r > rstart || south_bc)) {
             T extS[NT];
@@ -243,15 +249,22 @@ __global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const 
 #pragma unroll
                 for (int q = 0; q < NT; ++q) extS[q] = prevN[q];
             }
-#pragma unroll
-            for (int m = 0; m < NM; ++m) Lw[m] += (kS * T(lt.lj[m] * lt.sj[m])) * (extS[lt.mi[m]] - tS[lt.mi[m]]);
+            static_for<NM>([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+                constexpr double f = (2.0 * j + 1.0) * ((j % 2) ? -1.0 : 1.0);
+                Lw[m] += (kS * T(f)) * (extS[i] - tS[i]);
+            });
         }
 
         // the row below: its north face is this row's south face
         if (r > rstart && r - 1 >= r0 && r - 1 < r1) {
             if (inN) {
-#pragma unroll
-                for (int m = 0; m < NM; ++m) P[m] -= tdt * ((kN * T(lt.lj[m])) * (tS[lt.mi[m]] - prevN[lt.mi[m]]));
+                static_for<NM>([&](auto mc) {
+                    constexpr int m = decltype(mc)::value;
+                    constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+                    P[m] -= tdt * ((kN * T(2.0 * j + 1.0)) * (tS[i] - prevN[i]));
+                });
             }
             write_row(r - 1);
         }
@@ -262,8 +275,11 @@ __global__ void __launch_bounds__(256, CRK_LIN_MINB) step2d_linear_kernel(const 
                 if (inN) {
                     T extN[NT];
                     bc_trace(3, tN, extN);
-#pragma unroll
-                    for (int m = 0; m < NM; ++m) P[m] -= tdt * ((kN * T(lt.lj[m])) * (extN[lt.mi[m]] - tN[lt.mi[m]]));
+                    static_for<NM>([&](auto mc) {
+                        constexpr int m = decltype(mc)::value;
+                        constexpr int i = lin_mi<K, B>(m), j = lin_mj<K, B>(m);
+                        P[m] -= tdt * ((kN * T(2.0 * j + 1.0)) * (extN[i] - tN[i]));
+                    });
                 }
                 write_row(r);
             }
