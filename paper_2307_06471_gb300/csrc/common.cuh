@@ -285,6 +285,14 @@ __device__ __forceinline__ T tab_bT(const StepArgs& a, int i) {
 // arithmetic on launch parameters, is hoisted above it into the common path,
 // where it would run (predicated or speculated) on every row.
 __device__ __forceinline__ void cold_branch() { asm volatile("" ::: "memory"); }
+// v, opaque to the compiler: arithmetic on the result (boundary coordinates
+// and stage times from a row, column or stage index) cannot be speculated
+// above the cold branch that takes it, whatever the compiler assumes about
+// read-only loads and launch parameters
+__device__ __forceinline__ int opaque(int v) {
+    asm volatile("" : "+r"(v));
+    return v;
+}
 
 // f(std::integral_constant<int, i>) for i = 0 .. N-1: loops whose index must
 // be a constant expression (table entries folded at compile time)

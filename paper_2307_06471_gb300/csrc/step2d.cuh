@@ -447,7 +447,6 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             const bool need_L = i < S - 1;
             const bool need_flux = bi != T(0);
             if (!need_L && !need_flux) continue;
-            auto ti = [&]() { return t0 + tab_c(a, i) * dt; };   // boundary data only
             // stage state u^(i) = u^n - dt sum_{j<i} a_ij L_j
             T w[NV][NM];
 #pragma unroll
@@ -671,13 +670,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                             }
                     } else {
                         cold_branch();
+                        const int ryc = opaque(ry_), ic = opaque(i);
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
                             bc_exterior<T, NV>(bcw, 0, tWn[p], [&](double& x, double& y, double& t) {
                                 x = pv.x0();
-                                y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
-                                t = ti();
+                                y = pv.y0() + (ryc + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                                t = t0 + tab_c(a, ic) * dt;
                             }, ext);
 #pragma unroll
                             for (int v = 0; v < NV; ++v) tE[p][v] = edge ? ext[v] : tE[p][v];
@@ -697,13 +697,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                             }
                     } else {
                         cold_branch();
+                        const int ryc = opaque(ry_), ic = opaque(i);
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
                             bc_exterior<T, NV>(bce, 0, tE[p], [&](double& x, double& y, double& t) {
                                 x = pv.x0() + nx * pv.dx();
-                                y = pv.y0() + (ry_ + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
-                                t = ti();
+                                y = pv.y0() + (ryc + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
+                                t = t0 + tab_c(a, ic) * dt;
                             }, ext);
 #pragma unroll
                             for (int v = 0; v < NV; ++v) tWn[p][v] = edge ? ext[v] : tWn[p][v];
@@ -723,12 +724,13 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 T lo[NQ][NV];
                 if (south_bc) {   // row 0 without periodic wrap: boundary data (one uniform branch per row)
                     cold_branch();
+                    const int colc = opaque(col), ic = opaque(i);
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
                         bc_exterior<T, NV>(a.bc[2], 1, tS[p], [&](double& x, double& y, double& t) {
-                            x = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                            x = pv.x0() + (colc + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
                             y = pv.y0();
-                            t = ti();
+                            t = t0 + tab_c(a, ic) * dt;
                         }, lo[p]);
                 } else {
 #pragma unroll
@@ -864,6 +866,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         if (r == ny - 1 && !pery) {
             // top boundary: north face flux from the stored north traces
             cold_branch();
+            const int colc = opaque(col);
             T FN[NQ][NV];
 #pragma unroll
             for (int p = 0; p < NQ; ++p)
@@ -879,7 +882,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                     for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
                     bc_exterior<T, NV>(a.bc[3], 1, lo, [&](double& x, double& y, double& t) {
-                        x = pv.x0() + (col + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
+                        x = pv.x0() + (colc + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
                         y = pv.y0() + ny * pv.dy();
                         t = ti;
                     }, hi);
