@@ -344,9 +344,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
+            cold_branch();
             const int side = r < 0 ? 2 : 3;
+            const int colc = opaque(col);
             bc_exterior<T, NV>(a.bc[side], 1, own, [&](double& x, double& y, double& t) {
-                x = pv.x0() + (col + 0.5) * pv.dx();
+                x = pv.x0() + (colc + 0.5) * pv.dx();
                 y = r < 0 ? pv.y0() - 0.5 * pv.dy() : pv.y0() + (ny + 0.5) * pv.dy();
                 t = t0;
             }, out);
@@ -362,10 +364,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
             for (int v = 0; v < NV; ++v) out[v] = own[v];
         } else {
+            cold_branch();
             const int side = c < 0 ? 0 : 1;
+            const int rc = opaque(r);
             bc_exterior<T, NV>(a.bc[side], 0, own, [&](double& x, double& y, double& t) {
                 x = c < 0 ? pv.x0() - 0.5 * pv.dx() : pv.x0() + (nx + 0.5) * pv.dx();
-                y = pv.y0() + (r + 0.5) * pv.dy();
+                y = pv.y0() + (rc + 0.5) * pv.dy();
                 t = t0;
             }, out);
         }
