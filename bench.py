@@ -16,9 +16,11 @@ dt) -- one launch of the fused step kernel with dt read on the device.
 value  : DOF-updates/s = cells * 24 * K / (sum of per-step device times),
          CUDA events on the solver's stream around each step, L2 flushed
          (256 MiB write) between timed steps, outside the events.
-e2e    : the same metric through the C ABI with host buffers: upload of the
-         FP64 initial state from host memory, K x (crkdg_cfl_dt -> host,
-         crkdg_step(dt)), download of the FP64 state; wall clock.
+e2e    : the same metric through the C ABI with host buffers, wall clock:
+         upload of the FP64 initial state from pinned host memory, K
+         device-driven steps (dt from each step's own reduction) with each
+         step's run state (t, dt, max wave speed) read back asynchronously
+         into pinned memory, download of the FP64 state into pinned memory.
 --impl reference : the FP64 CPU oracle (numpy) on a bounded sample of the
          same workload (a 240 x 60 mesh of the same problem), timed on the
          host cores; rank 0 only.
@@ -343,8 +345,11 @@ def main():
         import crkdg_inputs as inp  # noqa: F401
         s2 = make_solver(estream.cuda_stream, nx, ny)
         s2.advance(args.warmup, WL["cfl"], WL["T"])
-        host = s2.get_state()                      # FP64 host state (input of the timed run)
-        out = np.empty_like(host)
+        # FP64 host state (input of the timed run) and the output buffer, both
+        # in pinned host memory
+        host = torch.empty(tuple(s2.shape), dtype=torch.float64, pin_memory=True).numpy()
+        s2.get_state(out=host)
+        out = torch.empty(tuple(s2.shape), dtype=torch.float64, pin_memory=True).numpy()
         mon = torch.zeros(args.steps, 5, dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -359,15 +364,15 @@ def main():
             s2.step_device()
             s2.run_state_async(mon[i].data_ptr())
         code2, _ = s2.sync()
-        out[...] = s2.get_state()
+        s2.get_state(out=out)
         wall = time.perf_counter() - t0
         assert code2 == 0 and bool((mon[:, 1] > 0).all())
         e2e = {"value": ws * dof * args.steps / wall, "unit": UNIT,
                "h2d_bytes_per_step": host.nbytes // args.steps,
                "d2h_bytes_per_step": 40 + out.nbytes // args.steps,
-               "note": "FP64 host state uploaded once (rounded to FP32 on the GPU), device-driven steps "
+               "note": "FP64 host state in pinned memory uploaded once (rounded to FP32 on the GPU), device-driven steps "
                        "(crkdg_step_device), the run state (t, dt, max wave speed) read back every step "
-                       "into pinned memory, state downloaded once (widened to FP64 on the GPU); bytes "
+                       "into pinned memory, state downloaded once into pinned memory (widened to FP64 on the GPU); bytes "
                        "per step = transfers / steps"}
         s2.close()
 

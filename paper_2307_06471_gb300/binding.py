@@ -229,10 +229,15 @@ class Solver:
         assert a.size == np.prod(self.shape)
         _check(lib().crkdg_set_state(self.ctx, _dptr(a), float(t)))
 
-    def get_state(self):
-        a = np.empty(self.shape)
-        _check(lib().crkdg_get_state(self.ctx, _dptr(a)))
-        return a
+    def get_state(self, out=None):
+        """The FP64 state as a new array, or written into `out` (a C-contiguous
+        float64 array of the state's shape, e.g. in pinned host memory)."""
+        if out is None:
+            out = np.empty(self.shape)
+        elif not (out.dtype == np.float64 and out.shape == tuple(self.shape) and out.flags["C_CONTIGUOUS"]):
+            raise ValueError("out must be a C-contiguous float64 array of shape %s" % (tuple(self.shape),))
+        _check(lib().crkdg_get_state(self.ctx, _dptr(out)))
+        return out
 
     def cfl_dt(self, cfl):
         d = C.c_double()

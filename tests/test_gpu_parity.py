@@ -273,6 +273,31 @@ def test_run_state_async_follows_device_driven_steps():
     assert r[-1, 0] == g.time()
 
 
+def test_state_round_trip_through_pinned_buffers():
+    """set_state from and get_state into pinned host buffers give the same
+    bytes as the pageable path, and a wrong output buffer is refused."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    bcs, st = _dmr_bcs()
+    gs, _ = make_pair_2d(40, 12, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, "f32")
+    gs.close()
+    g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32)
+    g.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
+    g.advance(2, 0.16, 0.2)
+    ref = g.get_state()
+    pin = torch.empty(tuple(g.shape), dtype=torch.float64, pin_memory=True).numpy()
+    assert g.get_state(out=pin) is pin
+    assert np.array_equal(pin, ref)
+    pin2 = torch.empty(tuple(g.shape), dtype=torch.float64, pin_memory=True).numpy()
+    g.set_state(pin, 0.25)
+    g.get_state(out=pin2)
+    assert np.array_equal(pin2, ref) and g.time() == 0.25
+    with pytest.raises(ValueError):
+        g.get_state(out=np.empty(tuple(g.shape), dtype=np.float32))
+    g.close()
+
+
 def test_autotune_keeps_the_state_and_caches(tmp_path):
     """crkdg_autotune with a limit pending (pass mode) leaves the run as it
     was: the next step of the tuned solver equals an untouched twin's bit for
