@@ -522,8 +522,8 @@ if __name__ == "__main__":
         r = advection1d()
     elif a.study == "advection2d":
         r = advection2d_inflow()
-    elif a.study == "advection_hbm":
-        r = advection_hbm()
+    elif a.study == "advection_hbm":   # --sizes N,steps (a smaller case, e.g. for a profiler)
+        r = advection_hbm(*(int(v) for v in a.sizes.split(",")[:2])) if a.sizes != "80,160,320" else advection_hbm()
     elif a.study == "dmr_full":
         r = dmr_full(*(int(v) for v in a.sizes.split(",")[:3])) if a.sizes != "80,160,320" else dmr_full()
     else:
