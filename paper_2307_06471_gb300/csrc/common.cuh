@@ -72,6 +72,14 @@ struct StepArgs {
     // (filled by set_limiter_params at its launch)
     float Mdx2f, Mdy2f, gammaf, pp_epsf;
     int tvb_on, pp_on;
+    // constants derived from the fields above, filled on the host by
+    // set_derived at every launch: no warp recomputes them (FP64 divisions
+    // run on GB300's narrow FP64 pipe, and every warp of a launch reaches its
+    // prologue at the same time)
+    double rx, ry, cell, adv_speed;   // 1/dx, 1/dy, dx dy, |bx|/dx + |by|/dy
+    float rxf, ryf, gm1f;
+    double lin_k[6];                  // modal step: 2bx/dx, 2by/dy, -bx/dx, bx/dx, -by/dy, by/dy
+    float lin_kf[6];
     const float* mlp;         // learned indicator parameters (device), or null
     float mlp_zlo, mlp_zhi;   // logit band in which the TVB test decides
 };
@@ -247,6 +255,26 @@ inline void set_limiter_params(StepArgs& a) {
     a.pp_on = a.pp_eps > 0.0;
 }
 
+// Every derived constant of a launch (the limiter parameters included), in
+// the same arithmetic the kernels would use: FP64, rounded once to FP32.
+inline void set_derived(StepArgs& a) {
+    set_limiter_params(a);
+    a.rx = 1.0 / a.dx;
+    a.ry = 1.0 / a.dy;
+    a.cell = a.dx * a.dy;
+    a.adv_speed = (a.beta[0] < 0 ? -a.beta[0] : a.beta[0]) / a.dx + (a.beta[1] < 0 ? -a.beta[1] : a.beta[1]) / a.dy;
+    a.rxf = (float)a.rx;
+    a.ryf = (float)a.ry;
+    a.gm1f = (float)(a.gamma - 1.0);
+    a.lin_k[0] = 2.0 * a.beta[0] / a.dx;
+    a.lin_k[1] = 2.0 * a.beta[1] / a.dy;
+    a.lin_k[2] = -a.beta[0] / a.dx;
+    a.lin_k[3] = a.beta[0] / a.dx;
+    a.lin_k[4] = -a.beta[1] / a.dy;
+    a.lin_k[5] = a.beta[1] / a.dy;
+    for (int i = 0; i < 6; ++i) a.lin_kf[i] = (float)a.lin_k[i];
+}
+
 // Device tableau buffer: FP64 a (MAXS x MAXS, row-major), b, c, followed by
 // FP32 copies of a and b rounded once on the host, so that FP32 kernels take
 // their stage weights without FP64 loads or conversions.
@@ -291,6 +319,14 @@ __device__ __forceinline__ void cold_branch() { asm volatile("" ::: "memory"); }
 // read-only loads and launch parameters
 __device__ __forceinline__ int opaque(int v) {
     asm volatile("" : "+r"(v));
+    return v;
+}
+__device__ __forceinline__ float opaque(float v) {
+    asm volatile("" : "+f"(v));
+    return v;
+}
+__device__ __forceinline__ double opaque(double v) {
+    asm volatile("" : "+d"(v));
     return v;
 }
 

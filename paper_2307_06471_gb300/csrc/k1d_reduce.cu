@@ -20,7 +20,9 @@ cudaError_t run_step1d(const StepArgs& a, int n_steps, int threads, int blocks, 
     });
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = (size_t)(a.s > 1 ? a.s - 1 : 1) * NDOF * sizeof(T) * threads;
-    kern<<<blocks, threads, smem, st>>>(a, n_steps);
+    StepArgs b = a;
+    set_derived(b);
+    kern<<<blocks, threads, smem, st>>>(b, n_steps);
     return cudaGetLastError();
 }
 

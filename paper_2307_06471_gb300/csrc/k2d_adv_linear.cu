@@ -20,7 +20,9 @@ cudaError_t run_linear(const StepArgs& a, int wpb, cudaStream_t st) {
     const int threads = wpb * 32;
     const size_t smem = (size_t)linear_smem_per_thread<T, K, B>(a.s) * sizeof(T) * threads;
     const int grid = (a.n_strips * a.n_segs + wpb - 1) / wpb;
-    kern<<<grid, threads, smem, st>>>(a);
+    StepArgs b = a;
+    set_derived(b);
+    kern<<<grid, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 

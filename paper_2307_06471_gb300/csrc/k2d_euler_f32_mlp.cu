@@ -21,7 +21,9 @@ cudaError_t run_step_mlp(const StepArgs& a, int wpb, cudaStream_t st) {
     const size_t smem = mlp_smem_offset<float, 2, B, PHYS_EULER>(a.s, threads) + mlp_smem_bytes(threads);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int total = a.n_strips * a.n_segs;
-    kern<<<(total + wpb - 1) / wpb, threads, smem, st>>>(a);
+    StepArgs b = a;
+    set_derived(b);
+    kern<<<(total + wpb - 1) / wpb, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 

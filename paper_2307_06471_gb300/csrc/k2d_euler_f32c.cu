@@ -22,7 +22,9 @@ cudaError_t run_step_c(const StepArgs& a, int wpb, cudaStream_t st) {
     const int threads = wpb * 32;
     const size_t smem = (size_t)C::smem_per_thread(a.s) * sizeof(float) * threads;
     const int total = a.n_strips * a.n_segs;
-    kern<<<(total + wpb - 1) / wpb, threads, smem, st>>>(a);
+    StepArgs b = a;
+    set_derived(b);
+    kern<<<(total + wpb - 1) / wpb, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 

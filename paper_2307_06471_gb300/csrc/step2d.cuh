@@ -112,6 +112,25 @@ struct ArgsView {
     __device__ __forceinline__ int* cur() const { return nullptr; }
     __device__ __forceinline__ unsigned* done() const { return nullptr; }
     __device__ __forceinline__ bool copy_if_idle() const { return true; }
+    // derived constants, computed on the host (set_derived)
+    __device__ __forceinline__ T rxT() const {
+        if constexpr (sizeof(T) == 4) return a.rxf;
+        else return T(a.rx);
+    }
+    __device__ __forceinline__ T ryT() const {
+        if constexpr (sizeof(T) == 4) return a.ryf;
+        else return T(a.ry);
+    }
+    __device__ __forceinline__ T Mdx2T() const {
+        if constexpr (sizeof(T) == 4) return a.Mdx2f;
+        else return T(a.M * a.dx * a.dx);
+    }
+    __device__ __forceinline__ T Mdy2T() const {
+        if constexpr (sizeof(T) == 4) return a.Mdy2f;
+        else return T(a.M * a.dy * a.dy);
+    }
+    __device__ __forceinline__ double cell() const { return a.cell; }
+    __device__ __forceinline__ double adv_speed() const { return a.adv_speed; }
 };
 
 template <class T>
@@ -145,6 +164,14 @@ struct ProbView {
     __device__ __forceinline__ int* cur() const { return cur_; }
     __device__ __forceinline__ unsigned* done() const { return done_; }
     __device__ __forceinline__ bool copy_if_idle() const { return false; }
+    // per-problem constants, in the arithmetic of set_derived
+    double M_, bx_, by_;
+    __device__ __forceinline__ T rxT() const { return T(1.0 / dx_); }
+    __device__ __forceinline__ T ryT() const { return T(1.0 / dy_); }
+    __device__ __forceinline__ T Mdx2T() const { return T(M_ * dx_ * dx_); }
+    __device__ __forceinline__ T Mdy2T() const { return T(M_ * dy_ * dy_); }
+    __device__ __forceinline__ double cell() const { return dx_ * dy_; }
+    __device__ __forceinline__ double adv_speed() const { return fabs(bx_) / dx_ + fabs(by_) / dy_; }
 };
 
 // FP64 epilogue of a step: warp reduction of the lane accumulators (max
@@ -295,6 +322,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         return;
     }
 
+    // launch constants: 1/dx, 1/dy and the limiter thresholds made on the host
+    // (set_derived), no FP64 division per warp
+    constexpr bool F32 = sizeof(T) == 4;
     Phys<T, PHYS> ph;
     if constexpr (PHYS == PHYS_EULER) {
         ph.gamma = T(a.gamma);
@@ -303,12 +333,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         ph.bx = T(a.beta[0]);
         ph.by = T(a.beta[1]);
     }
-    const T rx = T(1.0 / pv.dx()), ry = T(1.0 / pv.dy());
+    const T rx = opaque(pv.rxT()), ry = opaque(pv.ryT());   // held in registers, as when computed
     const T tdt = T(dt);
-    const T Mdx2 = T(a.M * pv.dx() * pv.dx()), Mdy2 = T(a.M * pv.dy() * pv.dy());
+    const T Mdx2 = pv.Mdx2T(), Mdy2 = pv.Mdy2T();
     const T gam = T(a.gamma);
-    const bool do_tvb = a.M >= 0.0, do_pp = a.pp_eps > 0.0;
-    const T pp_eps = T(a.pp_eps);
+    const bool do_tvb = a.tvb_on, do_pp = a.pp_on;
+    const T pp_eps = F32 ? T(a.pp_epsf) : T(a.pp_eps);
 
     // FP32 state: the per-cell wave speed and status tests of the epilogue run
     // in FP32 (GB300's FP64 pipe is 1/64 of its FP32 rate), the column totals
@@ -318,7 +348,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     T red_maxT = T(0);
 #pragma unroll
     for (int v = 0; v < NV; ++v) cs_hi[v] = cs_lo[v] = T(0);
-    const double adv_speed = PHYS == PHYS_EULER ? 0.0 : fabs(a.beta[0]) / pv.dx() + fabs(a.beta[1]) / pv.dy();
+    const double adv_speed = PHYS == PHYS_EULER ? 0.0 : pv.adv_speed();
 
     // reduction accumulators (FP64)
     double red_max = 0.0;
@@ -914,7 +944,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     }
 
     // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
-    const double cell = pv.dx() * pv.dy();
+    const double cell = pv.cell();
     if constexpr (F32R) {
         red_max = PHYS == PHYS_EULER ? double(red_maxT) : (outlane && r0 < r1 ? adv_speed : 0.0);
 #pragma unroll
@@ -975,6 +1005,9 @@ __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, con
     pv.y0_ = pb.y0;
     pv.dx_ = pb.dx;
     pv.dy_ = pb.dy;
+    pv.M_ = a.M;
+    pv.bx_ = a.beta[0];
+    pv.by_ = a.beta[1];
     pv.t_ = ds->t;
     pv.dt_ = ds->dt;
     pv.n_strips_ = pb.n_strips;

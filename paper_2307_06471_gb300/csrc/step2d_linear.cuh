@@ -105,13 +105,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CRK_LIN_MINB : 1) step2d
     }
 
     const T tdt = T(dt);
-    const T cx = T(2.0 * a.beta[0] / a.dx), cy = T(2.0 * a.beta[1] / a.dy);
+    // launch constants made on the host (set_derived): no FP64 divisions per warp
+    constexpr bool F32 = sizeof(T) == 4;
+    auto kc = [&](int i) -> T { return F32 ? T(a.lin_kf[i]) : T(a.lin_k[i]); };
+    const T cx = kc(0), cy = kc(1);
     // lifts of the inflow-face jumps: W (bx > 0), E (bx < 0), S (by > 0), N (by < 0)
     // integer flags (set on the host): tests on the FP64 launch parameters
     // would be re-evaluated on GB300's narrow FP64 pipe at every use
     const int inflow = a.lin_inflow;
     const bool inW = inflow & 1, inE = inflow & 2, inS = inflow & 4, inN = inflow & 8;
-    const T kW = T(-a.beta[0] / a.dx), kE = T(a.beta[0] / a.dx), kS = T(-a.beta[1] / a.dy), kN = T(a.beta[1] / a.dy);
+    const T kW = kc(2), kE = kc(3), kS = kc(4), kN = kc(5);
     const int S = a.s;
     // out = D w: the local operator (2 bx / dx) d/dxi + (2 by / dy) d/deta
     auto applyD = [&](const T* w, T* out) {
@@ -288,9 +291,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CRK_LIN_MINB : 1) step2d
         for (int q = 0; q < NT; ++q) prevN[q] = tN[q];
     }
 
-    double red_max = (outlane && r0 < r1) ? fabs(a.beta[0]) / a.dx + fabs(a.beta[1]) / a.dy : 0.0;
+    double red_max = (outlane && r0 < r1) ? a.adv_speed : 0.0;
     double red_sum[1] = {double(cs_hi) + double(cs_lo)};
-    step_epilogue<1, 3>(a, pv, gw, lane, total_warps, red_max, red_sum, 0u, status, a.dx * a.dy, t0, dt);
+    step_epilogue<1, 3>(a, pv, gw, lane, total_warps, red_max, red_sum, 0u, status, a.cell, t0, dt);
 }
 
 }  // namespace crk
