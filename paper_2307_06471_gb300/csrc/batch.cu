@@ -230,6 +230,8 @@ int crkdg_batch_create(const crkdg_batch_problem* probs, int n, const int* bc, i
         pb.y0 = q.y0;
         pb.dx = (q.x1 - q.x0) / q.nx;
         pb.dy = (q.y1 - q.y0) / q.ny;
+        pb.rx = 1.0 / pb.dx;
+        pb.ry = 1.0 / pb.dy;
         b->probs.push_back(pb);
         off += (size_t)q.nx * q.ny * b->nv * b->nm;
     }

@@ -164,10 +164,11 @@ struct ProbView {
     __device__ __forceinline__ int* cur() const { return cur_; }
     __device__ __forceinline__ unsigned* done() const { return done_; }
     __device__ __forceinline__ bool copy_if_idle() const { return false; }
-    // per-problem constants, in the arithmetic of set_derived
-    double M_, bx_, by_;
-    __device__ __forceinline__ T rxT() const { return T(1.0 / dx_); }
-    __device__ __forceinline__ T ryT() const { return T(1.0 / dy_); }
+    // per-problem constants, in the arithmetic of set_derived (1/dx and 1/dy
+    // from the problem table, made on the host)
+    double rx_, ry_, M_, bx_, by_;
+    __device__ __forceinline__ T rxT() const { return T(rx_); }
+    __device__ __forceinline__ T ryT() const { return T(ry_); }
     __device__ __forceinline__ T Mdx2T() const { return T(M_ * dx_ * dx_); }
     __device__ __forceinline__ T Mdy2T() const { return T(M_ * dy_ * dy_); }
     __device__ __forceinline__ double cell() const { return dx_ * dy_; }
@@ -979,6 +980,7 @@ struct BatchProblem {
     long long offset;      // element offset of the problem's planes in each buffer
     int nx, ny;
     double x0, y0, dx, dy;
+    double rx, ry;         // 1/dx, 1/dy (host)
     int n_strips, n_segs;
     int warp0;             // first task / reduction slot of the problem
 };
@@ -1005,6 +1007,8 @@ __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, con
     pv.y0_ = pb.y0;
     pv.dx_ = pb.dx;
     pv.dy_ = pb.dy;
+    pv.rx_ = pb.rx;
+    pv.ry_ = pb.ry;
     pv.M_ = a.M;
     pv.bx_ = a.beta[0];
     pv.by_ = a.beta[1];
