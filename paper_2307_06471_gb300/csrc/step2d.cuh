@@ -210,6 +210,10 @@ __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, i
     double mx = 0.0, sm_[NV], tr = 0.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
+    // the whole launch waits for this loop: unrolled so that the loads of
+    // several slots are in flight together (each lane's additions keep their
+    // order, so the result does not change)
+#pragma unroll 8
     for (int wi = lane; wi < total_warps; wi += 32) {
         const double* q = pv.partials() + (size_t)wi * NRED;
         mx = fmax(mx, __ldcg(q));
