@@ -144,26 +144,32 @@ int max_wpb(crkdg_ctx* c) {
     return std::min(8, std::min(by_regs, by_smem));
 }
 
-int default_launch(crkdg_ctx* c) {
-    if (c->dim != 2) return CRKDG_OK;
+// Segment rows for which the step kernel's warps fill the resident slots of
+// the 152 SMs `waves` times over (registers and private shared memory of the
+// kernel decide the slots; blocks of w warps), segments of >= 8 rows.
+int wave_rows(crkdg_ctx* c, int w, int waves, int* rows) {
     const int ns = (c->mesh.nx + 29) / 30;
-    int w = max_wpb(c);
-    if (w < 0) return w;
-    c->wpb = std::min(w, 4);
-    // one wave: as many warps as the 152 SMs hold at once (registers and
-    // private shared memory of the step kernel decide), segments of >= 8 rows
     crk::KernelInfo ki;
     CK(crk::info_step2d(c->kphys, c->precision, c->k, c->basis, c->tab.s, &ki));
     const int regs_warp = ((ki.regs + 7) / 8) * 8 * 32;
     const int by_regs = 65536 / regs_warp;
     const int by_smem = (228 * 1024) / std::max(1, ki.smem_per_thread * 32);
     int resident = std::min(64, std::min(by_regs, by_smem));
-    resident = std::max(c->wpb, resident / c->wpb * c->wpb);
-    const long target = 152L * resident;
+    resident = std::max(w, resident / w * w);
+    const long target = 152L * resident * waves;
     const long nseg = std::max(1L, target / ns);
     int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
-    c->seg_rows = std::min(L, c->mesh.ny);
+    *rows = std::min(L, c->mesh.ny);
     return CRKDG_OK;
+}
+
+int default_launch(crkdg_ctx* c) {
+    if (c->dim != 2) return CRKDG_OK;
+    int w = max_wpb(c);
+    if (w < 0) return w;
+    c->wpb = std::min(w, 4);
+    // one wave: as many warps as the SMs hold at once
+    return wave_rows(c, c->wpb, 1, &c->seg_rows);
 }
 
 int enqueue_reduce(crkdg_ctx* c, int set_dt) {
@@ -974,8 +980,32 @@ int crkdg_autotune(crkdg_ctx* c, double* best_us) {
     CK(cudaStreamSynchronize(c->stream));
     const int mx = max_wpb(c);
     if (mx < 0) return mx;
+    // candidates: the current shape first (tuning never makes it worse), the
+    // one- and two-wave shapes of every block size, then a fixed ladder
     const int rows[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96};
     const int wpbs[] = {1, 2, 4, 8};
+    std::vector<std::pair<int, int>> cand;
+    auto add = [&](int L, int w) {
+        L = std::max(1, std::min(L, c->mesh.ny));
+        for (auto& p : cand)
+            if (p.first == L && p.second == w) return;
+        cand.emplace_back(L, w);
+    };
+    add(c->seg_rows, c->wpb);
+    for (int w : wpbs) {
+        if (w > mx) continue;
+        for (int waves = 1; waves <= 2; ++waves) {
+            int L = 0;
+            int r = wave_rows(c, w, waves, &L);
+            if (r) return r;
+            add(L, w);
+        }
+    }
+    for (int L : rows) {
+        if (L > c->mesh.ny && L != rows[0]) continue;
+        for (int w : wpbs)
+            if (w <= mx) add(L, w);
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -995,11 +1025,10 @@ int crkdg_autotune(crkdg_ctx* c, double* best_us) {
         CK(cudaMemcpy(&ms, &c->d_state->maxspeed, sizeof(double), cudaMemcpyDeviceToHost));
         dt = ms > 0 ? 0.05 / ms : 1e-6;
     }
-    for (int L : rows) {
-        if (L > c->mesh.ny && L != rows[0]) continue;
-        for (int w : wpbs) {
-            if (w > mx) continue;
-            c->seg_rows = std::min(L, c->mesh.ny);
+    for (const auto& cw : cand) {
+        {
+            const int w = cw.second;
+            c->seg_rows = cw.first;
             c->wpb = w;
             float t[6];
             for (int it = 0; it < 6; ++it) {
