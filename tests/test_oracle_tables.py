@@ -1,10 +1,9 @@
 """Pins of the oracle against the numbers the paper prints (Tables 1.1,
 4.1--4.5).  Fixtures under tests/golden/ cite their table.
 
-Agreement bands (readings recorded in the design doc): the paper does not state its
-quadrature, norm sample points, final-step handling or LLF variant, so values
-are compared within a relative band per table, and convergence orders within
-0.05 of the printed ones.  Table 4.4 (linear, tableau-independent) is matched
+Agreement bands: the paper does not state its quadrature, norm sample points,
+final-step handling or LLF variant, so values are compared within a relative
+band per table, and convergence orders within 0.05 of the printed ones.  Table 4.4 (linear, tableau-independent) is matched
 to 1 %."""
 import os
 
