@@ -23,7 +23,9 @@ cudaError_t run_linear(const StepArgs& a, int wpb, cudaStream_t st) {
     StepArgs b = a;
     set_derived(b);
     kern<<<grid, threads, smem, st>>>(b);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize<1>(b, st);
 }
 
 template <class T, int K, int B>

@@ -24,7 +24,9 @@ cudaError_t run_step_mlp(const StepArgs& a, int wpb, cudaStream_t st) {
     StepArgs b = a;
     set_derived(b);
     kern<<<(total + wpb - 1) / wpb, threads, smem, st>>>(b);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize<4>(b, st);
 }
 
 }  // namespace

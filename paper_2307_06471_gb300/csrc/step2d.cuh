@@ -112,6 +112,7 @@ struct ArgsView {
     __device__ __forceinline__ int* cur() const { return nullptr; }
     __device__ __forceinline__ unsigned* done() const { return nullptr; }
     __device__ __forceinline__ bool copy_if_idle() const { return true; }
+    static constexpr bool kLastWarp = false;   // finalize_step_kernel ends the step
     // derived constants, computed on the host (set_derived)
     __device__ __forceinline__ T rxT() const {
         if constexpr (sizeof(T) == 4) return a.rxf;
@@ -164,6 +165,7 @@ struct ProbView {
     __device__ __forceinline__ int* cur() const { return cur_; }
     __device__ __forceinline__ unsigned* done() const { return done_; }
     __device__ __forceinline__ bool copy_if_idle() const { return false; }
+    static constexpr bool kLastWarp = true;    // the problem's last warp ends its step
     // per-problem constants, in the arithmetic of set_derived (1/dx and 1/dy
     // from the problem table, made on the host)
     double rx_, ry_, M_, bx_, by_;
@@ -175,15 +177,41 @@ struct ProbView {
     __device__ __forceinline__ double adv_speed() const { return fabs(bx_) / dx_ + fabs(by_) / dy_; }
 };
 
+// Device run-state update after a step from the reduced slots: t, the next
+// dt = min(cfl / max speed, t_end - t), totals, troubled count.
+__device__ __forceinline__ void finish_run_state(const StepArgs& a, DevState* ds, double mx, const double* sm_,
+                                                 int nv, double tr, double t0, double dt, int* cur,
+                                                 unsigned* done) {
+    ds->maxspeed = mx;
+    for (int v = 0; v < nv; ++v) ds->sums[v] = sm_[v];
+    // troubled cells: this step's limit-on-load, else a separate pass over u^n
+    ds->troubled = a.limit ? tr : double(ds->lim_count);
+    ds->lim_count = 0;
+    const double tn = t0 + dt;
+    ds->t = tn;
+    double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
+    const double rem = ds->t_end - tn;
+    const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
+    if (dn > rem) dn = rem;
+    if (reached) dn = 0.0;
+    ds->dt = dn;
+    ds->steps += 1;
+    ds->counter = 0;
+    if (cur) *cur ^= 1;
+    if (done && reached) atomicAdd(done, 1u);
+}
+
 // FP64 epilogue of a step: warp reduction of the lane accumulators (max
-// wave speed, NV totals, troubled count, status bits) into the warp's slot,
-// then the last warp to arrive (atomic counter, no waiting) reduces all slots
-// in a fixed order and updates the device run state: t, the next dt =
-// min(cfl / max speed, t_end - t), totals, troubled count.
+// wave speed, NV totals, troubled count, status bits) into the warp's slot
+// (NV + 2 doubles).  Single problems (PV::kLastWarp false) leave the rest to
+// finalize_step_kernel, launched after the step; in a batch the last warp of
+// a problem to arrive (atomic counter, no waiting) reduces that problem's
+// slots in a fixed order and updates its run state.
 template <int NV, int NRED, class PV>
 __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, int gw, int lane, int total_warps,
                                               double red_max, double* red_sum, unsigned red_trouble,
                                               unsigned status, double cell, double t0, double dt) {
+    static_assert(NRED == NV + 2, "slot layout: max speed, NV totals, troubled count");
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         red_max = fmax(red_max, __shfl_xor_sync(0xffffffffu, red_max, off));
@@ -200,55 +228,96 @@ __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, i
         for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
         slotp[1 + NV] = double(red_trouble);
         if (status) atomicOr(&pv.ds()->status, status);
-        __threadfence();
-        prev = atomicAdd(&pv.ds()->counter, 1u);
+        if constexpr (PV::kLastWarp) {
+            __threadfence();
+            prev = atomicAdd(&pv.ds()->counter, 1u);
+        }
     }
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != (unsigned)total_warps - 1) return;
-    // last warp: fixed-order reduction of all per-warp slots (deterministic)
-    __threadfence();
+    if constexpr (!PV::kLastWarp) {
+        return;
+    } else {
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev != (unsigned)total_warps - 1) return;
+        // last warp: fixed-order reduction of all per-warp slots (deterministic)
+        __threadfence();
+        double mx = 0.0, sm_[NV], tr = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
+        for (int wi = lane; wi < total_warps; wi += 32) {
+            const double* q = pv.partials() + (size_t)wi * NRED;
+            mx = fmax(mx, __ldcg(q));
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
+            tr += __ldcg(q + 1 + NV);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
+            tr += __shfl_xor_sync(0xffffffffu, tr, off);
+        }
+        if (lane == 0) finish_run_state(a, pv.ds(), mx, sm_, NV, tr, t0, dt, pv.cur(), pv.done());
+    }
+}
+
+// The end of a single-problem step, as its own launch of one block (the
+// step's slots are complete when it starts): every thread loads its few
+// slots at once, a fixed-order tree (deterministic) reduces them, and thread
+// 0 updates the device run state.  A waiting last warp of the step itself
+// would reduce ~1,000-2,400 slots alone while the rest of the GPU idles.
+constexpr int FINALIZE_THREADS = 512;
+template <int NV>
+__global__ void __launch_bounds__(FINALIZE_THREADS) finalize_step_kernel(const StepArgs a, int total_warps) {
+    constexpr int NRED = NV + 2;
+    DevState* ds = a.ds;
+    const double t0 = a.dt_from_dev ? ds->t : a.t;
+    const double dt = a.dt_from_dev ? ds->dt : a.dt;
+    if (!(dt > 0.0)) return;   // the step left the state and the run state unchanged
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double mx = 0.0, sm_[NV], tr = 0.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
-    // the whole launch waits for this loop: unrolled so that the loads of
-    // several slots are in flight together (each lane's additions keep their
-    // order, so the result does not change)
-#pragma unroll 8
-    for (int wi = lane; wi < total_warps; wi += 32) {
-        const double* q = pv.partials() + (size_t)wi * NRED;
-        mx = fmax(mx, __ldcg(q));
+    for (int wi = threadIdx.x; wi < total_warps; wi += FINALIZE_THREADS) {
+        const double* q = a.partials + (size_t)wi * NRED;
+        mx = fmax(mx, q[0]);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
-        tr += __ldcg(q + 1 + NV);
+        for (int v = 0; v < NV; ++v) sm_[v] += q[1 + v];
+        tr += q[1 + NV];
     }
+    auto warp_tree = [&]() {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        for (int off = 16; off > 0; off >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
-        tr += __shfl_xor_sync(0xffffffffu, tr, off);
-    }
+            for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
+            tr += __shfl_xor_sync(0xffffffffu, tr, off);
+        }
+    };
+    warp_tree();
+    __shared__ double red[FINALIZE_THREADS / 32][NRED];
     if (lane == 0) {
-        DevState* ds = pv.ds();
-        ds->maxspeed = mx;
+        red[w][0] = mx;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ds->sums[v] = sm_[v];
-        // troubled cells: this step's limit-on-load, else a separate pass over u^n
-        ds->troubled = a.limit ? tr : double(ds->lim_count);
-        ds->lim_count = 0;
-        const double tn = t0 + dt;
-        ds->t = tn;
-        double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
-        const double rem = ds->t_end - tn;
-        const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
-        if (dn > rem) dn = rem;
-        if (reached) dn = 0.0;
-        ds->dt = dn;
-        ds->steps += 1;
-        ds->counter = 0;
-        if (pv.cur()) *pv.cur() ^= 1;
-        if (pv.done() && reached) atomicAdd(pv.done(), 1u);
+        for (int v = 0; v < NV; ++v) red[w][1 + v] = sm_[v];
+        red[w][1 + NV] = tr;
     }
+    __syncthreads();
+    if (w != 0) return;
+    constexpr int NW = FINALIZE_THREADS / 32;
+    mx = lane < NW ? red[lane][0] : 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm_[v] = lane < NW ? red[lane][1 + v] : 0.0;
+    tr = lane < NW ? red[lane][1 + NV] : 0.0;
+    warp_tree();
+    if (lane == 0) finish_run_state(a, ds, mx, sm_, NV, tr, t0, dt, nullptr, nullptr);
+}
+
+// launch of finalize_step_kernel after a single-problem step launched with b
+template <int NV>
+inline cudaError_t launch_finalize(const StepArgs& b, cudaStream_t st) {
+    finalize_step_kernel<NV><<<1, FINALIZE_THREADS, 0, st>>>(b, b.n_strips * b.n_segs);
+    return cudaGetLastError();
 }
 
 // COMP = true: compensated FP32 state.  The buffers hold hi planes followed

@@ -303,9 +303,10 @@ def compact(nx=1920, ny=480, steps=100, precision="f32"):
         sim = s.time() - t0
         out[name] = {"cfl": cfl, "ms_per_step": ms / steps, "sim_time": sim,
                      "device_ms_per_unit_time": ms / sim, "status": s.sync()[1],
-                     # cRKDG: limiter pass + fused step; RKDG: 3 x (limiter pass, DG
-                     # forward-Euler pass) + 2 linear combinations + the time update
-                     "launches_per_step": 2 if name == "crkdg" else 9,
+                     # cRKDG: limiter pass + fused step + its one-block finalize; RKDG:
+                     # 3 x (limiter pass, DG forward-Euler pass + finalize) + 2 linear
+                     # combinations + the time update
+                     "launches_per_step": 3 if name == "crkdg" else 12,
                      "operator_passes_per_step": 1 if name == "crkdg" else 3,
                      "limiter_passes_per_step": 1 if name == "crkdg" else 3}
         s.close()
