@@ -179,19 +179,20 @@ struct ProbView {
 
 // Device run-state update after a step from the reduced slots: t, the next
 // dt = min(cfl / max speed, t_end - t), totals, troubled count.
+// cfl, t_end, lim_count: the run state's values (not written by the step)
 __device__ __forceinline__ void finish_run_state(const StepArgs& a, DevState* ds, double mx, const double* sm_,
-                                                 int nv, double tr, double t0, double dt, int* cur,
-                                                 unsigned* done) {
+                                                 int nv, double tr, double t0, double dt, double cfl,
+                                                 double t_end, unsigned lim_count, int* cur, unsigned* done) {
     ds->maxspeed = mx;
     for (int v = 0; v < nv; ++v) ds->sums[v] = sm_[v];
     // troubled cells: this step's limit-on-load, else a separate pass over u^n
-    ds->troubled = a.limit ? tr : double(ds->lim_count);
+    ds->troubled = a.limit ? tr : double(lim_count);
     ds->lim_count = 0;
     const double tn = t0 + dt;
     ds->t = tn;
-    double dn = ds->cfl > 0.0 && mx > 0.0 ? ds->cfl / mx : dt;
-    const double rem = ds->t_end - tn;
-    const bool reached = rem <= 1e-12 * fmax(1.0, fabs(ds->t_end));
+    double dn = cfl > 0.0 && mx > 0.0 ? cfl / mx : dt;
+    const double rem = t_end - tn;
+    const bool reached = rem <= 1e-12 * fmax(1.0, fabs(t_end));
     if (dn > rem) dn = rem;
     if (reached) dn = 0.0;
     ds->dt = dn;
@@ -226,7 +227,7 @@ __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, i
         slotp[0] = red_max;
 #pragma unroll
         for (int v = 0; v < NV; ++v) slotp[1 + v] = red_sum[v] * cell;
-        slotp[1 + NV] = double(red_trouble);
+        slotp[1 + NV] = __longlong_as_double((long long)red_trouble);   // an integer, stored bitwise
         if (status) atomicOr(&pv.ds()->status, status);
         if constexpr (PV::kLastWarp) {
             __threadfence();
@@ -248,7 +249,7 @@ __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, i
             mx = fmax(mx, __ldcg(q));
 #pragma unroll
             for (int v = 0; v < NV; ++v) sm_[v] += __ldcg(q + 1 + v);
-            tr += __ldcg(q + 1 + NV);
+            tr += double(__double_as_longlong(__ldcg(q + 1 + NV)));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -257,68 +258,125 @@ __device__ __forceinline__ void step_epilogue(const StepArgs& a, const PV& pv, i
             for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
             tr += __shfl_xor_sync(0xffffffffu, tr, off);
         }
-        if (lane == 0) finish_run_state(a, pv.ds(), mx, sm_, NV, tr, t0, dt, pv.cur(), pv.done());
+        if (lane == 0) {
+            DevState* ds = pv.ds();
+            finish_run_state(a, ds, mx, sm_, NV, tr, t0, dt, ds->cfl, ds->t_end, ds->lim_count, pv.cur(), pv.done());
+        }
     }
 }
 
 // The end of a single-problem step, as its own launch of one block (the
-// step's slots are complete when it starts): every thread loads its few
-// slots at once, a fixed-order tree (deterministic) reduces them, and thread
-// 0 updates the device run state.  A waiting last warp of the step itself
-// would reduce ~1,000-2,400 slots alone while the rest of the GPU idles.
-constexpr int FINALIZE_THREADS = 512;
+// step's slots are complete when it starts): each thread reduces a run of
+// slots with their loads in flight together, then fixed-order trees
+// (deterministic); thread 0 updates the device run state.  A last warp of the
+// step itself would reduce ~1,000-2,400 slots alone while the rest of the GPU
+// idles.  The block runs on one SM, whose FP64 pipe (1/64 of the FP32 rate)
+// would bound it: only the NV totals are added in FP64; the maximum wave
+// speed is taken on the bit patterns (non-negative doubles order as integers)
+// and the troubled count is an integer.
+constexpr int FINALIZE_THREADS = 256;
+
+// a slot's speed as an ordered key: NaN (ignored, as fmax does) and -0 map to 0
+__device__ __forceinline__ unsigned long long speed_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const bool neg = b >> 63, nan = (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+    return neg || nan ? 0ull : b;
+}
+
 template <int NV>
 __global__ void __launch_bounds__(FINALIZE_THREADS) finalize_step_kernel(const StepArgs a, int total_warps) {
     constexpr int NRED = NV + 2;
+    // launched as a programmatic dependent of the step: wait here until the
+    // step grid has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     DevState* ds = a.ds;
+    // every load is issued before any result is needed: the run state (none
+    // of these fields is written by the step) and the thread's slots
     const double t0 = a.dt_from_dev ? ds->t : a.t;
     const double dt = a.dt_from_dev ? ds->dt : a.dt;
-    if (!(dt > 0.0)) return;   // the step left the state and the run state unchanged
+    const double cfl = ds->cfl, t_end = ds->t_end;
+    const unsigned lim_count = ds->lim_count;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double mx = 0.0, sm_[NV], tr = 0.0;
+    unsigned long long mk = 0, tr = 0;
+    double sm_[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) sm_[v] = 0.0;
-    for (int wi = threadIdx.x; wi < total_warps; wi += FINALIZE_THREADS) {
-        const double* q = a.partials + (size_t)wi * NRED;
-        mx = fmax(mx, q[0]);
+    // chunks of PER slots per thread, loaded unconditionally from valid
+    // addresses (slot 0 past the end, masked) so that all are in flight at once
+    constexpr int PER = 8;
+    for (int base = threadIdx.x; base < total_warps; base += PER * FINALIZE_THREADS) {
+        double qv[PER][NRED];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sm_[v] += q[1 + v];
-        tr += q[1 + NV];
+        for (int k = 0; k < PER; ++k) {
+            const int wi = base + k * FINALIZE_THREADS;
+            const double* q = a.partials + (size_t)(wi < total_warps ? wi : 0) * NRED;
+#pragma unroll
+            for (int e = 0; e < NRED; ++e) qv[k][e] = q[e];
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (base + k * FINALIZE_THREADS >= total_warps) break;
+            const unsigned long long key = speed_key(qv[k][0]);
+            mk = key > mk ? key : mk;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm_[v] += qv[k][1 + v];
+            tr += (unsigned long long)__double_as_longlong(qv[k][1 + NV]);
+        }
     }
     auto warp_tree = [&]() {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+            const unsigned long long k = __shfl_xor_sync(0xffffffffu, mk, off);
+            mk = k > mk ? k : mk;
 #pragma unroll
             for (int v = 0; v < NV; ++v) sm_[v] += __shfl_xor_sync(0xffffffffu, sm_[v], off);
             tr += __shfl_xor_sync(0xffffffffu, tr, off);
         }
     };
+    if (!(dt > 0.0)) return;   // the step left the state and the run state unchanged
     warp_tree();
-    __shared__ double red[FINALIZE_THREADS / 32][NRED];
+    constexpr int NW = FINALIZE_THREADS / 32;
+    __shared__ unsigned long long red_k[NW], red_t[NW];
+    __shared__ double red_s[NW][NV];
     if (lane == 0) {
-        red[w][0] = mx;
+        red_k[w] = mk;
+        red_t[w] = tr;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) red[w][1 + v] = sm_[v];
-        red[w][1 + NV] = tr;
+        for (int v = 0; v < NV; ++v) red_s[w][v] = sm_[v];
     }
     __syncthreads();
     if (w != 0) return;
-    constexpr int NW = FINALIZE_THREADS / 32;
-    mx = lane < NW ? red[lane][0] : 0.0;
+    mk = lane < NW ? red_k[lane] : 0ull;
+    tr = lane < NW ? red_t[lane] : 0ull;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sm_[v] = lane < NW ? red[lane][1 + v] : 0.0;
-    tr = lane < NW ? red[lane][1 + NV] : 0.0;
+    for (int v = 0; v < NV; ++v) sm_[v] = lane < NW ? red_s[lane][v] : 0.0;
     warp_tree();
-    if (lane == 0) finish_run_state(a, ds, mx, sm_, NV, tr, t0, dt, nullptr, nullptr);
+    if (lane == 0)
+        finish_run_state(a, ds, __longlong_as_double((long long)mk), sm_, NV, double(tr), t0, dt, cfl, t_end, lim_count,
+                         nullptr, nullptr);
 }
 
-// launch of finalize_step_kernel after a single-problem step launched with b
+// launch of finalize_step_kernel after a single-problem step launched with b,
+// as a programmatic dependent launch: the step's blocks allow it early
+// (griddepcontrol.launch_dependents), so its block is scheduled as soon as an
+// SM has room and only waits for the step's completion, without a launch gap
 template <int NV>
 inline cudaError_t launch_finalize(const StepArgs& b, cudaStream_t st) {
-    finalize_step_kernel<NV><<<1, FINALIZE_THREADS, 0, st>>>(b, b.n_strips * b.n_segs);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(FINALIZE_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, finalize_step_kernel<NV>, b, b.n_strips * b.n_segs);
 }
+
+// In a step kernel: its dependent finalize launch may be scheduled now
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 // COMP = true: compensated FP32 state.  The buffers hold hi planes followed
 // by lo planes (u = hi + lo); every stage computes in T from hi, and only the
@@ -1038,6 +1096,7 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MIN
         mlp_load_smem(mw, a.mlp);
         __syncthreads();
     }
+    allow_dependent_launch();
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
     const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? CRK_LIN_MINB : 1) step2d
     const int tid = threadIdx.x;
     const int lane = tid & 31;
 
+    allow_dependent_launch();
     const int gw = blockIdx.x * (nthr >> 5) + (tid >> 5);
     const int total_warps = a.n_strips * a.n_segs;
     if (gw >= total_warps) return;   // whole warp leaves; no block barriers
