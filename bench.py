@@ -9,9 +9,10 @@ limiter M = 50 once per step followed by the positivity-preserving scaling
 reductions, CFL 0.16.  Synthetic: the analytic initial data, advanced W
 warm-up steps before timing.
 
-A "step" is one full cRKDG time step (limit-on-load, all inner stages, the
-final DG stage with boundary data, the FP64 reductions that give the next
-dt) -- one launch of the fused step kernel with dt read on the device.
+A "step" is one full cRKDG time step (the previous step's limiter, all inner
+stages, the final DG stage with boundary data, the FP64 reductions that give
+the next dt) -- three launches: the limiter pass, the fused step kernel with
+dt read on the device, and its one-block finalize (slot reduction, next dt).
 
 value  : DOF-updates/s = cells * 24 * K / (sum of per-step device times),
          CUDA events on the solver's stream around each step, L2 flushed
