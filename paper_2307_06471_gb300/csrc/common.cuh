@@ -309,14 +309,15 @@ __device__ __forceinline__ T tab_bT(const StepArgs& a, int i) {
     else return tab_b(a, i);
 }
 
-// Entry of a rarely taken branch (boundary data): no memory access, and so no
-// arithmetic on launch parameters, is hoisted above it into the common path,
-// where it would run (predicated or speculated) on every row.
+// Entry of a rarely taken branch (boundary data): no ordinary memory access is
+// hoisted above it into the common path, where it would run (predicated or
+// speculated) on every row.  Arithmetic on launch parameters and read-only
+// loads can still move across it; the branch's indices pass through opaque().
 __device__ __forceinline__ void cold_branch() { asm volatile("" ::: "memory"); }
-// v, opaque to the compiler: arithmetic on the result (boundary coordinates
-// and stage times from a row, column or stage index) cannot be speculated
-// above the cold branch that takes it, whatever the compiler assumes about
-// read-only loads and launch parameters
+// v, opaque to the compiler.  In a cold branch: arithmetic on the result
+// (boundary coordinates and stage times from a row, column or stage index)
+// cannot be speculated above the branch.  On a launch constant: the value is
+// held in a register from that point, as a computed one would be.
 __device__ __forceinline__ int opaque(int v) {
     asm volatile("" : "+r"(v));
     return v;
