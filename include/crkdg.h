@@ -222,8 +222,10 @@ int crkdg_run_state_async(crkdg_ctx* ctx, double* out);
 /* Launch shape of the fused 2D step: rows per warp segment and warps per
  * block (0 = keep).  crkdg_autotune times candidates on the current state
  * (run state restored afterwards; a limit pending in CRKDG_LIMIT_PASS mode is
- * applied first, as the next step would apply it) and keeps the fastest;
- * returns its time per step kernel in microseconds.  Synchronises. */
+ * applied first, as the next step would apply it) and keeps the fastest; the
+ * candidates include the current shape, so tuning never selects a shape
+ * slower in its own timing.  Returns the kept shape's time per step (the step
+ * kernel and its one-block finalize) in microseconds.  Synchronises. */
 int crkdg_set_launch(crkdg_ctx* ctx, int seg_rows, int warps_per_block);
 int crkdg_get_launch(const crkdg_ctx* ctx, int* seg_rows, int* warps_per_block);
 int crkdg_autotune(crkdg_ctx* ctx, double* best_us);
