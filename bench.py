@@ -47,14 +47,20 @@ SAMPLE = dict(nx=240, ny=60)      # bounded oracle sample of the same problem
 
 # ncu dram traffic of the step kernel for this workload, per launch, and the
 # hash of the kernel sources it was taken with (None until captured)
-TRAFFIC = {"bytes": 136974080, "src_hash": "a031a04061328df3"}
+TRAFFIC = {"bytes": 136974080, "src_hash": "43275bdad3954e68"}
 
 
 def kernel_src_hash():
+    """Hash of the step kernel's sources without their comments: a change of
+    code (not of a comment) voids the recorded traffic."""
+    import re
     h = hashlib.sha256()
     for f in ("step2d.cuh", "common.cuh", "limiter.cuh", "tables.cuh"):
-        with open(os.path.join(ROOT, "paper_2307_06471_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2307_06471_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", " ", src).encode())
     return h.hexdigest()[:16]
 
 

@@ -26,7 +26,7 @@ struct DevState {
     double sums[4];
     double troubled;          // troubled cells flagged in the last step
     unsigned status;          // ST_* bits
-    unsigned counter;         // arrival counter of the last-warp reduction
+    unsigned counter;         // arrival counter of a batched problem's last-warp reduction
     unsigned long long steps;
     unsigned long long lim_count;   // cells flagged by a separate limiter pass since the last step
 };

@@ -19,7 +19,8 @@
 // of exchanged: the compactness of cRKDG (Sec. 3.1) means one ring suffices.
 // Boundary data enter only the final-stage fluxes, at t^n + c_i dt (Sec. 3.4).
 // The FP64 epilogue reduces the new cell averages (max wave speed, totals;
-// eq. (3.4)) with a last-warp-done pass and updates the device run state.
+// eq. (3.4)) per warp; finalize_step_kernel (a batch: the problem's last warp)
+// combines the warps' slots and updates the device run state.
 #pragma once
 #include "common.cuh"
 #include "limiter.cuh"
@@ -1075,7 +1076,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         }
     }
 
-    // ---- FP64 reductions: warp -> per-warp slot -> last warp -------------------------
+    // ---- FP64 reductions: warp -> per-warp slot -> finalize (batch: last warp) -------
     const double cell = pv.cell();
     if constexpr (F32R) {
         red_max = PHYS == PHYS_EULER ? double(red_maxT) : (outlane && r0 < r1 ? adv_speed : 0.0);
