@@ -140,3 +140,56 @@ def test_positivity_scaling_invariants():
     assert np.array_equal(v[..., 0], bad[..., 0])
     rho, _, p = dg.phys.primitive(np.einsum("yxvm,qm->yxqv", v, P))
     assert rho.min() >= 1e-10 * (1 - 1e-6) and p.min() >= 1e-10 * (1 - 1e-3) - 1e-12
+
+
+def _x_profile_state(avg, a1, nm=6, ny=3, hi=0.1):
+    """Scalar P^2 state on a periodic 4 x 3 mesh of [0,1]^2, constant in y:
+    cell averages avg[x], x-slope coefficients a1[x], y-slopes 0, every
+    second-degree mode hi."""
+    u = np.zeros((ny, len(avg), 1, nm))
+    for x in range(len(avg)):
+        u[:, x, 0, 0] = avg[x]
+        u[:, x, 0, 1] = a1[x]
+    u[..., 3:] = hi
+    return u
+
+
+@pytest.mark.parametrize("M,flagged,slopes", [
+    # worked by hand (periodic, dx = 1/4): cell 0 sees differences (+1, -6),
+    # cell 1 (+2, +1), cell 2 (+3, +2), cell 3 (-6, +3)
+    (0.0, [True, True, False, True], [0.0, 1.0, 1.0, 0.0]),
+    # M dx^2 = 0.25: |a1| = 0.2 of cell 3 is below it and stays
+    (4.0, [True, True, False, False], [0.0, 1.0, 1.0, -0.2]),
+])
+def test_scalar_tvb_minmod_worked_example(M, flagged, slopes):
+    dg = DG2D(4, 3, (0, 1, 0, 1), 2, "P", Advection([1.0, 0.0]), PER)
+    u = _x_profile_state([0.0, 1.0, 3.0, 6.0], [0.5, 2.0, 1.0, -0.2])
+    v, flags = tvb_limit(dg, u, M, 0.0)
+    assert np.array_equal(flags, np.tile(np.array(flagged), (3, 1)))
+    for x in range(4):
+        assert np.all(v[:, x, 0, 1] == slopes[x])
+        assert np.all(v[:, x, 0, 2] == 0.0)                       # y-slopes stay 0
+        assert np.all(v[:, x, 0, 3:] == (0.0 if flagged[x] else 0.1))
+        assert np.all(v[:, x, 0, 0] == u[:, x, 0, 0])
+
+
+def test_euler_entropy_wave_limits_like_scalar_density():
+    """At rest with uniform pressure, a density-only profile lies entirely in
+    the entropy field (its left eigenvector row is (1, 0, 0, -b1) with the
+    energy slope 0, the acoustic rows vanish on it), so the characteristic
+    limiter acts on the density slope exactly as the scalar minmod and leaves
+    momentum and energy slopes at 0."""
+    dg = DG2D(4, 3, (0, 1, 0, 1), 2, "P", Euler(1.4, 2), PER)
+    avg_rho = [1.0, 2.0, 4.0, 7.0]
+    a1 = [0.5, 2.0, 1.0, -0.2]
+    u = np.zeros((3, 4, 4, 6))
+    for x in range(4):
+        u[:, x, :, 0] = inp.conserved(avg_rho[x], 0.0, 0.0, 1.0)
+        u[:, x, 0, 1] = a1[x]
+    v, flags = tvb_limit(dg, u, 0.0, 0.0)
+    assert np.array_equal(flags, np.tile(np.array([True, True, False, True]), (3, 1)))
+    want = [0.0, 1.0, 1.0, 0.0]
+    for x in range(4):
+        assert np.allclose(v[:, x, 0, 1], want[x], rtol=0, atol=1e-12)
+        assert np.allclose(v[:, x, 1:, 1], 0.0, rtol=0, atol=1e-12)
+        assert np.allclose(v[:, x, :, 2], 0.0, rtol=0, atol=1e-12)
