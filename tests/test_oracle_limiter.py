@@ -126,6 +126,41 @@ def test_positivity_scaling_closed_form_density():
     assert np.array_equal(v[..., 0], u[..., 0])
 
 
+def test_positivity_scaling_closed_form_pressure():
+    """theta_2 from a quadratic worked by hand.  P^1 state with averages
+    rho = 1, rho w = 1, rho v = 0, E = 0.6 (p = 0.04) and xi-slopes
+    d rho = 0.3, d(rho w) = 0.8 (all other slopes 0).  Along the segment
+    ubar + t (u_q - ubar) to a point with xi = 1 (every east-face point)
+        rho(t) = 1 + 0.3 t,   rho w(t) = 1 + 0.8 t,   E(t) = 0.6,
+    and p(t) = eps, i.e. rho (E - k) - (rho w)^2 / 2 = 0 with k = eps/(gamma-1):
+        (1 + 0.3 t)(0.6 - k) - (1 + 0.8 t)^2 / 2 = 0
+        <=>  0.32 t^2 + (0.8 - 0.3 (0.6 - k)) t - (0.1 - k) = 0.
+    A point with xi = x in (0, 1) reaches the same state at t / x, later; the
+    west points (xi < 0) have positive pressure (rho w < 1 there), and the
+    density stays >= 0.7, so theta_1 = 1 and theta_2 is the positive root.
+    Every non-constant mode of every variable is scaled by theta_2."""
+    from oracle.limiter import positivity_limit, positivity_points
+    dg = DG2D(1, 1, (0, 1, 0, 1), 1, "P", Euler(1.4, 2), PER)
+    eps = 1e-3
+    k = eps / 0.4
+    u = np.zeros((1, 1, 4, 3))
+    u[0, 0, :, 0] = (1.0, 1.0, 0.0, 0.6)
+    u[0, 0, 0, 1] = 0.3
+    u[0, 0, 1, 1] = 0.8
+    a, b, c = 0.32, 0.8 - 0.3 * (0.6 - k), -(0.1 - k)
+    theta = (-b + np.sqrt(b * b - 4 * a * c)) / (2 * a)
+    assert 0.1 < theta < 0.2
+    v = positivity_limit(dg, u, eps)
+    assert np.array_equal(v[..., 0], u[..., 0])
+    assert v[0, 0, 0, 1] == pytest.approx(0.3 * theta, rel=1e-12)
+    assert v[0, 0, 1, 1] == pytest.approx(0.8 * theta, rel=1e-12)
+    assert np.all(v[0, 0, 2:, 1:] == 0.0) and np.all(v[0, 0, :2, 2] == 0.0)
+    # the east-face points land on p = eps exactly, no point below it
+    rho, _, p = dg.phys.primitive(np.einsum("yxvm,qm->yxqv", v, positivity_points(dg)))
+    assert p.min() == pytest.approx(eps, rel=1e-9)
+    assert rho.min() > 0.9
+
+
 def test_positivity_scaling_invariants():
     from oracle.limiter import positivity_limit, positivity_points
     dg = _euler_dg(n=12)
