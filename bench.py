@@ -73,12 +73,13 @@ def dmr_mesh(B, inp, nx, ny):
     return B.make_mesh(2, nx, ny, WL["box"], bc, fn, params), st
 
 
-def make_solver(stream_handle, nx, ny):
+def make_solver(stream_handle, nx, ny, precision="f32"):
     import crkdg_inputs as inp
     from paper_2307_06471_gb300 import binding as B
     from paper_2307_06471_gb300 import tableaux as GTB
     mesh, st = dmr_mesh(B, inp, nx, ny)
-    s = B.Solver(mesh, WL["k"], B.BASIS_P, GTB.BY_NAME[WL["tab"]], B.EULER, B.F32, stream=stream_handle)
+    s = B.Solver(mesh, WL["k"], B.BASIS_P, GTB.BY_NAME[WL["tab"]], B.EULER, B.F32 if precision == "f32" else B.F64,
+                 stream=stream_handle)
     s.project_function(lambda X, Y: inp.dmr_ic(X, Y, st))
     s.limit(WL["M"])
     s.positivity(WL["pp_eps"])
@@ -139,6 +140,44 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alu_peaks(stream_handle):
+    """FP32 (scalar and packed FP32x2) and FP64 FMA peaks of this GPU,
+    measured by the library's FMA probe (crkdg_alu_peak) just before the
+    timed region."""
+    from paper_2307_06471_gb300 import binding as B
+    out = {}
+    for name, kind in (("f32", B.PEAK_F32), ("f32x2", B.PEAK_F32X2), ("f64", B.PEAK_F64)):
+        tf, ms, sms = B.alu_peak(kind, reps=9, stream=stream_handle)
+        out[name] = {"tflops": tf, "ms_per_launch": ms}
+    out["sms"] = sms
+    return out
+
+
+def timed_steps(s, stream, flush, steps, use_pass):
+    """Device times (ms) of `steps` whole steps, each bracketed by CUDA events
+    on the solver's stream, L2 flushed before each (outside the events):
+    (total, mean limiter pass, mean step kernel + finalize)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[i].record(stream)
+        if use_pass:
+            s.apply_limit()        # limiter pass of the previous step's final stage (in place)
+        mids[i].record(stream)
+        s.step_device()            # fused cRKDG step kernel + its one-block finalize
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    lim = sum(a.elapsed_time(b) for a, b in zip(starts, mids)) / steps
+    ker = sum(a.elapsed_time(b) for a, b in zip(mids, ends)) / steps
+    return total, lim, ker
 
 
 def measured_peaks():
@@ -267,6 +306,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm of the same workload")
+    ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--limit-mode", default="pass", choices=["pass", "fused"],
                     help="pending limiter as a separate pass before the step kernel, or fused into its load")
     args = ap.parse_args()
@@ -299,29 +340,16 @@ def main():
     seg_rows, wpb = s.get_launch()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    # measured FP32 / FP64 FMA peaks (the roofline's denominator), before the
+    # timed region
+    alu = alu_peaks(stream.cuda_stream)
     # warm-up: device-driven steps (first dt from a reduction of the state)
     s.advance(args.warmup, WL["cfl"], WL["T"])
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            starts[i].record(stream)
-            if use_pass:
-                s.apply_limit()        # limiter pass of the previous step's final stage (in place)
-            mids[i].record(stream)
-            s.step_device()            # fused cRKDG step kernel + its one-block finalize
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    lim_ms = sum(a.elapsed_time(b) for a, b in zip(starts, mids)) / args.steps
-    step_kernel_ms = sum(a.elapsed_time(b) for a, b in zip(mids, ends)) / args.steps
+        dev_ms, lim_ms, step_kernel_ms = timed_steps(s, stream, flush, args.steps, use_pass)
     code, status = s.sync()
     t_sim = s.time()
     dev_ms, value, _ = aggregate(dev_ms, dof, args.steps)
@@ -333,8 +361,7 @@ def main():
     bpc = step_bytes_per_cell(WL["k"], WL["basis"], "euler", 4)
     clocks = clk.summary()
     peaks, peak_kind = measured_peaks()
-    mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    fp32_peak = alu["f32"]["tflops"]              # measured: FP32 FMA probe on this GPU
     # roofline of the dominant kernel (the fused step) from its own event-timed
     # duration; the limiter pass is HBM bound: it reads the 24 modes of every
     # cell (neighbour averages hit L1/L2) and rewrites only the limited cells
@@ -383,6 +410,23 @@ def main():
                        "per step = transfers / steps"}
         s2.close()
 
+    # the same workload in FP64 on the GPU (the reference precision): the
+    # same state after the warm-up, device-timed the same way
+    fp64_arm = None
+    if not args.no_fp64:
+        s64 = make_solver(stream.cuda_stream, nx, ny, precision="f64")
+        s64.set_limit_mode(B.LIMIT_PASS if use_pass else B.LIMIT_FUSED)
+        s64.advance(args.warmup, WL["cfl"], WL["T"])
+        n64 = min(args.steps, args.fp64_steps)
+        t64, l64, k64 = timed_steps(s64, stream, flush, n64, use_pass)
+        c64, st64 = s64.sync()
+        fp64_arm = {"value": dof * n64 / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64 / n64, "steps": n64,
+                    "limit_pass_ms": l64 if use_pass else None, "step_kernel_ms": k64, "status": st64,
+                    "fp32_speedup": (t64 / n64) / ms_per_step,
+                    "note": "CRKDG_F64: the same DMR workload and launch sequence with an FP64 state and FP64 "
+                            "arithmetic (GB300's FP64 FMA rate is the f64 entry of alu_peaks)"}
+        s64.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, sec, n = oracle_sample(SAMPLE["nx"], SAMPLE["ny"], 8)
@@ -405,10 +449,12 @@ def main():
                                                  "(reduction of the per-warp slots, next dt)",
                              "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                              "frac": achieved / fp32_peak, "traffic": traffic,
-                             "peak_note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x %.0f MHz (%s max clock)"
-                                          % (mhz, peak_kind),
-                             "flop_per_cell": fpc, "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / peaks["hbm_gbs"]},
-                "limit_pass": limit_pass,
+                             "peak_note": "measured: FP32 FMA probe (crkdg_alu_peak, scalar FFMA chains, %d SMs, "
+                                          "median of 9 launches) on this GPU just before the timed region"
+                                          % alu["sms"],
+                             "flop_per_cell": fpc, "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / peaks["hbm_gbs"],
+                             "hbm_peak_source": peak_kind},
+                "limit_pass": limit_pass, "alu_peaks": alu, "fp64_arm": fp64_arm,
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * (3 if use_pass else 2),
                 "status": {"code": code, "bits": status, "t_sim": t_sim},
                 "cpu_baseline": cpu}

@@ -76,12 +76,28 @@ enum { CRKDG_FN_CONST = 0, CRKDG_FN_SINE = 1, CRKDG_FN_SINE_PROD = 2, CRKDG_FN_D
 enum { CRKDG_SIDE_W = 0, CRKDG_SIDE_E = 1, CRKDG_SIDE_S = 2, CRKDG_SIDE_N = 3 };
 enum { CRKDG_ADVECTION = 0, CRKDG_EULER = 1 };
 enum { CRKDG_BASIS_P = 0, CRKDG_BASIS_Q = 1 };
-/* CRKDG_F32C: compensated FP32 state, 2D Euler without limiters.  The state
- * is kept as hi + lo FP32 pairs; all stage arithmetic runs in FP32 on hi and
- * only the final update u^{n+1} = u^n + Delta is accumulated exactly, which
- * removes the per-step rounding of the state itself (the FP32 error of the
- * increments is O(eps dt) per step, cf. the perturbed-RK result of Sec. 3.3). */
-enum { CRKDG_F32 = 0, CRKDG_F64 = 1, CRKDG_F32C = 2 };
+/* Precision of the state and of the step's arithmetic.
+ * CRKDG_F32   FP32 state and arithmetic, FP64 reductions.
+ * CRKDG_F64   FP64 throughout.
+ * CRKDG_F32C  compensated FP32 state, 2D Euler without limiters.  The state
+ *             is kept as hi + lo FP32 pairs; all stage arithmetic runs in
+ *             FP32 on hi and only the final update u^{n+1} = u^n + Delta is
+ *             accumulated exactly (TwoSum), which removes the per-step
+ *             rounding of the state itself; Delta keeps the FP32 rounding of
+ *             the fluxes, O(eps |f|) per point.
+ * CRKDG_F32D  compensated FP32 state with deviation-form fluxes, 2D Euler
+ *             without limiters: every stage state is held as its deviation
+ *             from the cell's base state (the hi part of its average) and
+ *             every flux as f(c + d) - f(c) by exact algebraic differences,
+ *             so the inner-stage operators, the final stage and Delta carry
+ *             FP32 errors of a few ulps of their own size.  The final stage
+ *             is then evaluated to full accuracy in the sense of the
+ *             perturbed-RK estimate of Sec. 3.3 (Grant), at FP32 speed, and
+ *             the run keeps the convergence order of FP64 (boundary data of
+ *             non-affine Dirichlet sides are formed from FP32-rounded full
+ *             states: exact deviations on periodic, outflow, wall and
+ *             constant-state sides only).  Same planes as CRKDG_F32C. */
+enum { CRKDG_F32 = 0, CRKDG_F64 = 1, CRKDG_F32C = 2, CRKDG_F32D = 3 };
 enum { CRKDG_FLUX_LLF = 0 };   /* Lax--Friedrichs, alpha per face point and stage */
 
 typedef struct {
@@ -112,7 +128,8 @@ typedef struct crkdg_ctx crkdg_ctx;   /* opaque; owns all device buffers */
  *   tab        explicit Butcher tableau, 1 <= s <= CRKDG_MAX_STAGES
  *   gamma      ratio of specific heats (Euler)
  *   physics    CRKDG_ADVECTION (phys_params = beta_x, beta_y) or CRKDG_EULER
- *   precision  CRKDG_F32 (bulk FP32, FP64 reductions) or CRKDG_F64
+ *   precision  CRKDG_F32 (bulk FP32, FP64 reductions), CRKDG_F64, or the
+ *              compensated forms CRKDG_F32C / CRKDG_F32D (2D Euler)
  *   stream     cudaStream_t to run on (NULL: the legacy default stream)
  * Allocates the state (two ping-pong copies) and scratch on the current
  * device.  Returns CRKDG_EINVAL / CRKDG_EUNSUPPORTED / CRKDG_ENOMEM. */
@@ -359,6 +376,22 @@ int crkdg_features(crkdg_ctx* ctx, float* X_dev, float* y_dev, double M_tvb);
  * 2D Euler, k = 2, FP32; net must outlive its use. */
 int crkdg_set_indicator(crkdg_ctx* ctx, const crkdg_mlp* net, double z_lo, double z_hi);
 
+/* Measured arithmetic peak of the current device (no counterpart in the
+ * paper: the denominator of the step kernel's roofline, which is bound by
+ * FP32 fused multiply-adds rather than by memory).  A grid of 8 warps' worth
+ * of blocks per SM runs 8 independent FMA chains per thread; the median of
+ * `reps` launches timed by CUDA events on `stream` (NULL: legacy default
+ * stream; synchronises) gives
+ *   tflops         FMA flops (2 per FMA; 4 per packed FP32x2 FMA) per second / 1e12,
+ *   ms_per_launch  the median launch time (may be NULL),
+ *   n_sms          the SM count the grid covered (may be NULL).
+ * kind: CRKDG_PEAK_F32 (scalar FFMA), CRKDG_PEAK_F32X2 (packed __ffma2_rn),
+ * CRKDG_PEAK_F64 (DFMA).  Allocates a few KiB for a result sink.  Errors:
+ * crkdg_probe_last_error(). */
+enum { CRKDG_PEAK_F32 = 0, CRKDG_PEAK_F32X2 = 1, CRKDG_PEAK_F64 = 2 };
+int crkdg_alu_peak(int kind, int reps, void* stream, double* tflops, double* ms_per_launch, int* n_sms);
+const char* crkdg_probe_last_error(void);
+
 /* No-allocation reduction (no counterpart in the paper; an interface for
  * callers that cannot allocate device memory: code inside a framework that
  * owns the device memory pool, or code that must not allocate while a graph
@@ -368,17 +401,28 @@ int crkdg_set_indicator(crkdg_ctx* ctx, const crkdg_mlp* net, double z_lo, doubl
  * terms) and the totals sum_K |K| ubar_K, without allocating:
  *   u_dev    device state planes [v][m][y][x] of n_modes modes (caller-owned,
  *            FP32 or FP64 per `precision`), only read;
- *   out_dev  device array of 1 + nv doubles (caller-owned): out[0] = max wave
- *            speed, out[1 + v] = total of variable v; written on `stream`;
+ *   dim      1 or 2; in 1D ny and dy are ignored (one row of unit height,
+ *            as crkdg_create lays out a 1D mesh);
+ *   out_dev  device array of 2 + nv doubles (caller-owned), written on
+ *            `stream`: out[0] = max wave speed, out[1 + v] = total of
+ *            variable v, out[1 + nv] = the status bits the reduction saw
+ *            (an integer value: CRKDG_ST_NONPHYSICAL for a cell average with
+ *            rho <= 0 or p <= 0, CRKDG_ST_NAN for a NaN wave speed; 0 when
+ *            the state is physical) -- a NaN cell does not show in out[0],
+ *            since the maximum skips NaN, so check out[1 + nv];
  *   beta     host pointer to (beta_x, beta_y) for advection, else may be NULL.
  * Asynchronous on `stream`.  Scratch: a file-scope device array of about
  * 64 KiB (1024 per-warp slots) that every GPU loading the library holds until
- * the process exits; the first call on each device looks up its address with
- * that device current (so make that first call before any stream capture).
- * Every call shares the array and clears its counter first, so calls that
- * overlap on the GPU (other streams, other threads) race: serialise them.
- * Meshes above 2^30 cells are rejected with CRKDG_EINVAL; errors are reported
- * by crkdg_noalloc_last_error().  Calls no cudaMalloc/cudaFree. */
+ * the process exits.  Its device address is looked up, with the stream's
+ * device current, at every call made outside a stream capture; a call made
+ * while `stream` is being captured reuses the address of the last uncaptured
+ * call on that device, so the first call on a device must come before any
+ * capture (CRKDG_EINVAL otherwise), and after cudaDeviceReset make one
+ * uncaptured call before capturing again.  Every call shares the array and
+ * clears its counter first, so calls that overlap on the GPU (other streams,
+ * other threads) race: serialise them.  Meshes above 2^30 cells are rejected
+ * with CRKDG_EINVAL; errors are reported by crkdg_noalloc_last_error().
+ * Calls no cudaMalloc/cudaFree. */
 int crkdg_reduce_state_noalloc(const void* u_dev, int dim, int nx, int ny, int n_modes, int physics, int precision,
                                double dx, double dy, double gamma, const double* beta, double* out_dev,
                                void* stream);

@@ -22,7 +22,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_DIRICHLET = 0, 1, 2, 3
 FN_CONST, FN_SINE, FN_SINE_PROD, FN_DMR_BOTTOM, FN_DMR_TOP = 0, 1, 2, 3, 4
 ADVECTION, EULER = 0, 1
 BASIS_P, BASIS_Q = 0, 1
-F32, F64, F32C = 0, 1, 2
+F32, F64, F32C, F32D = 0, 1, 2, 3
 LIMIT_FUSED, LIMIT_PASS = 0, 1
 FORM_QUADRATURE, FORM_AUTO = 0, 1
 FLUX_LLF = 0
@@ -84,6 +84,9 @@ _SIGS = {
                                              C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                                              C.c_void_p, C.c_void_p]),
     "crkdg_noalloc_last_error": (C.c_char_p, []),
+    "crkdg_alu_peak": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_int)]),
+    "crkdg_probe_last_error": (C.c_char_p, []),
     "crkdg_last_error": (C.c_char_p, []),
     "crkdg_version": (C.c_char_p, []),
     "crkdg_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(Tableau),
@@ -148,6 +151,19 @@ def _check(code):
 
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+PEAK_F32, PEAK_F32X2, PEAK_F64 = 0, 1, 2
+
+
+def alu_peak(kind, reps=7, stream=None):
+    """(TFLOP/s, median ms per launch, SMs) of the FMA probe crkdg_alu_peak."""
+    tf, ms, n = C.c_double(), C.c_double(), C.c_int()
+    code = lib().crkdg_alu_peak(int(kind), int(reps), C.c_void_p(stream) if stream else None, C.byref(tf),
+                                C.byref(ms), C.byref(n))
+    if code != 0:
+        raise CrkdgError(code, lib().crkdg_probe_last_error().decode())
+    return tf.value, ms.value, n.value
 
 
 def make_tableau(A, b):
@@ -325,7 +341,7 @@ class Solver:
         c = self.config
         return "%dx%d/k%d%s/s%d/%s/%s/limit%d/%s" % (
             self.mesh.nx, self.mesh.ny, c["k"], "PQ"[c["basis"]], c["stages"],
-            "euler" if c["physics"] == EULER else "advection", ("f32", "f64", "f32c")[c["precision"]],
+            "euler" if c["physics"] == EULER else "advection", ("f32", "f64", "f32c", "f32d")[c["precision"]],
             self.get_limit_mode(), torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu")
 
     def autotune(self, cache=None):

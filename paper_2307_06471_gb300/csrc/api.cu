@@ -87,6 +87,9 @@ struct crkdg_ctx {
 
 namespace {
 
+// hi + lo FP32 planes: the compensated state, with or without deviation fluxes
+bool compensated(int precision) { return precision == CRKDG_F32C || precision == CRKDG_F32D; }
+
 int n_modes(int dim, int k, int basis) {
     if (dim == 1) return k + 1;
     return basis == CRKDG_BASIS_P ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 1);
@@ -145,7 +148,7 @@ int max_wpb(crkdg_ctx* c) {
 }
 
 // Segment rows for which the step kernel's warps fill the resident slots of
-// the 152 SMs `waves` times over (registers and private shared memory of the
+// the device's SMs `waves` times over (registers and private shared memory of the
 // kernel decide the slots; blocks of w warps), segments of >= 8 rows.
 int wave_rows(crkdg_ctx* c, int w, int waves, int* rows) {
     const int ns = (c->mesh.nx + 29) / 30;
@@ -156,7 +159,7 @@ int wave_rows(crkdg_ctx* c, int w, int waves, int* rows) {
     const int by_smem = (228 * 1024) / std::max(1, ki.smem_per_thread * 32);
     int resident = std::min(64, std::min(by_regs, by_smem));
     resident = std::max(w, resident / w * w);
-    const long target = 152L * resident * waves;
+    const long target = (long)std::max(1, crk::sm_count()) * resident * waves;
     const long nseg = std::max(1L, target / ns);
     int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
     *rows = std::min(L, c->mesh.ny);
@@ -173,7 +176,7 @@ int default_launch(crkdg_ctx* c) {
 }
 
 int enqueue_reduce(crkdg_ctx* c, int set_dt) {
-    const int blocks = 4 * 152;
+    const int blocks = 4 * std::max(1, crk::sm_count());
     int r = ensure_partials(c, (size_t)blocks * 8 * 8);
     if (r) return r;
     CK(crk::launch_reduce(c->dim, c->kphys, c->precision, c->u[c->cur], c->mesh.nx, c->dim == 1 ? 1 : c->mesh.ny, c->nm,
@@ -186,7 +189,7 @@ int enqueue_reduce(crkdg_ctx* c, int set_dt) {
 // affine (outflow, wall, constant state), not switched off
 bool use_linear(const crkdg_ctx* c) {
     if (c->op_form != CRKDG_FORM_AUTO || c->kphys != crk::PHYS_ADV || c->dim != 2 ||
-        c->precision == CRKDG_F32C)
+        compensated(c->precision))
         return false;
     crk::BCSide bc[4];
     for (int s = 0; s < 4; ++s) {
@@ -201,7 +204,7 @@ bool use_linear(const crkdg_ctx* c) {
 }
 
 // one wave of the modal step: as many warps as its registers and shared
-// memory let the 152 SMs hold, segments of >= 8 rows
+// memory let the device's SMs hold, segments of >= 8 rows
 int linear_shape(crkdg_ctx* c) {
     if (c->lin_seg_rows > 0) return CRKDG_OK;
     crk::KernelInfo ki;
@@ -213,7 +216,7 @@ int linear_shape(crkdg_ctx* c) {
     int resident = std::min(64, std::min(by_regs, by_smem));
     resident = std::max(wpb, resident / wpb * wpb);
     const int ns = (c->mesh.nx + 29) / 30;
-    const long nseg = std::max(1L, 152L * resident / ns);
+    const long nseg = std::max(1L, (long)std::max(1, crk::sm_count()) * resident / ns);
     const int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
     c->lin_seg_rows = std::min(L, c->mesh.ny);
     c->lin_wpb = wpb;
@@ -347,9 +350,9 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
     if (basis != CRKDG_BASIS_P && basis != CRKDG_BASIS_Q) return fail(CRKDG_EINVAL, "basis must be P or Q");
     if (flux != CRKDG_FLUX_LLF) return fail(CRKDG_EINVAL, "flux must be CRKDG_FLUX_LLF");
     if (physics != CRKDG_ADVECTION && physics != CRKDG_EULER) return fail(CRKDG_EINVAL, "unknown physics");
-    if (precision != CRKDG_F32 && precision != CRKDG_F64 && precision != CRKDG_F32C)
+    if (precision != CRKDG_F32 && precision != CRKDG_F64 && !compensated(precision))
         return fail(CRKDG_EINVAL, "unknown precision");
-    if (precision == CRKDG_F32C && (physics != CRKDG_EULER || mesh->dim != 2))
+    if (compensated(precision) && (physics != CRKDG_EULER || mesh->dim != 2))
         return fail(CRKDG_EUNSUPPORTED, "the compensated FP32 state is built for 2D Euler");
     if (tab->s < 1 || tab->s > CRKDG_MAX_STAGES) return fail(CRKDG_EINVAL, "tableau stages must be 1..6");
     for (int i = 0; i < tab->s; ++i)
@@ -395,7 +398,7 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
     c->ncell = (size_t)c->mesh.nx * c->mesh.ny;
     c->elems = c->ncell * c->nv * c->nm;
     c->esize = precision == CRKDG_F64 ? 8 : 4;
-    c->planes = precision == CRKDG_F32C ? 2 : 1;   // compensated: hi planes then lo planes
+    c->planes = compensated(precision) ? 2 : 1;   // compensated: hi planes then lo planes
     c->kphys = physics == CRKDG_ADVECTION ? crk::PHYS_ADV : (mesh->dim == 1 ? crk::PHYS_EULER1D : crk::PHYS_EULER);
     c->stream = static_cast<cudaStream_t>(stream);
     c->t = 0.0;
@@ -696,7 +699,7 @@ static int enqueue_limit_buf(crkdg_ctx* c, void* u, double t, double M, double p
 
 int crkdg_rkdg_step(crkdg_ctx* c, double dt, int order) {
     if (check_ctx(c)) return CRKDG_EINVAL;
-    if (c->dim != 2 || c->precision == CRKDG_F32C) return fail(CRKDG_EUNSUPPORTED, "RKDG is built for 2D FP32/FP64");
+    if (c->dim != 2 || compensated(c->precision)) return fail(CRKDG_EUNSUPPORTED, "RKDG is built for 2D FP32/FP64");
     if (order != 2 && order != 3) return fail(CRKDG_EINVAL, "order must be 2 or 3 (Shu--Osher SSP forms)");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(CRKDG_EINVAL, "dt must be positive and finite");
     if (!c->u3) {
@@ -780,7 +783,7 @@ int crkdg_run_fixed(crkdg_ctx* c, int n_steps, double dt) {
 int crkdg_limit(crkdg_ctx* c, double M) {
     if (check_ctx(c)) return CRKDG_EINVAL;
     if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "the TVB limiter is built for 2D meshes");
-    if (c->precision == CRKDG_F32C && M >= 0.0)
+    if (compensated(c->precision) && M >= 0.0)
         return fail(CRKDG_EUNSUPPORTED, "limiters are not built for the compensated FP32 state");
     if (M >= 0.0) {
         c->limiter_on = true;
@@ -799,7 +802,7 @@ int crkdg_positivity(crkdg_ctx* c, double eps) {
     if (check_ctx(c)) return CRKDG_EINVAL;
     if (c->dim != 2 || c->physics != CRKDG_EULER)
         return fail(CRKDG_EUNSUPPORTED, "positivity scaling is built for 2D Euler");
-    if (c->precision == CRKDG_F32C && eps > 0.0)
+    if (compensated(c->precision) && eps > 0.0)
         return fail(CRKDG_EUNSUPPORTED, "limiters are not built for the compensated FP32 state");
     if (eps > 0.0) {
         c->pp_eps = eps;
@@ -831,7 +834,7 @@ int crkdg_set_indicator(crkdg_ctx* c, const crkdg_mlp* net, double z_lo, double 
 
 int crkdg_features(crkdg_ctx* c, float* X_dev, float* y_dev, double M) {
     if (check_ctx(c) || !X_dev || !y_dev) return fail(CRKDG_EINVAL, "null argument");
-    if (c->dim != 2 || c->physics != CRKDG_EULER || c->precision == CRKDG_F32C)
+    if (c->dim != 2 || c->physics != CRKDG_EULER || compensated(c->precision))
         return fail(CRKDG_EUNSUPPORTED, "features are built for 2D Euler FP32/FP64 states");
     if (!(M >= 0.0)) return fail(CRKDG_EINVAL, "M must be >= 0");
     if (!c->t_known) {

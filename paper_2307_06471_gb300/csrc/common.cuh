@@ -147,6 +147,96 @@ template <class T> struct Phys<T, PHYS_EULER1D> {
     }
 };
 
+// 2D Euler fluxes in deviation form.  A state is held as its deviation d
+// from a base state c (per cell: the FP32 high part of the cell's average at
+// t^n), and every flux as the deviation f(c + d) - f(c), computed from
+// exact algebraic differences in which each term is a base or full quantity
+// times a deviation:
+//   du = (d_m - u0 d_rho) / rho1,  dv = (d_n - v0 d_rho) / rho1,
+//   d(m u) = d_m u0 + m1 du,  d(n v) = d_n v0 + n1 dv,
+//   dp = (gamma - 1)(d_E - (d(m u) + d(n v)) / 2),
+//   d((E + p) u) = (d_E + dp) u0 + (E1 + p1) du,  ...
+// with u0 = m0 / rho0 (any rounding of u0 only perturbs a term that is
+// already multiplied by a deviation), m1 = m0 + d_m, E1 + p1 = E0 + p0 +
+// d_E + dp.  The FP32 rounding error of a flux is then a few ulps of the
+// deviation, O(eps |f(u) - f(c)|) = O(eps h |f_x|), instead of a few ulps of
+// the flux itself, O(eps |f|).  A DG operator applied to deviation fluxes
+// equals the operator applied to the fluxes (the constant f(c) has zero
+// discrete divergence: the Gauss rules integrate grad phi_m and phi_m on the
+// faces exactly), so div^loc f and div^DG f come out with errors relative to
+// their own size, as Sec. 3.3's perturbed-RK estimate assumes of a
+// full-accuracy final stage.  Only the base changes from cell to cell:
+// face states and face fluxes are moved between two cells' bases by the
+// deviation of the base difference.
+template <class T>
+struct EulerDev {
+    static constexpr int NV = 4;
+    T gm1, gamma;
+    T r0, u0, v0, m0, n0, p0, ep0;   // base: rho, velocity, momentum, pressure, E + p
+    __device__ __forceinline__ void set_base(const T* c) {
+        r0 = c[0];
+        m0 = c[1];
+        n0 = c[2];
+        const T ir = T(1) / c[0];
+        u0 = c[1] * ir;
+        v0 = c[2] * ir;
+        p0 = gm1 * (c[3] - T(0.5) * (c[1] * u0 + c[2] * v0));
+        ep0 = c[3] + p0;
+    }
+    // the deviation's primitive increments: 1 / rho1, du, dv, d(m u), d(n v), dp, m1, n1
+    struct Inc {
+        T r1i, du, dv, dmu, dnv, dp, m1, n1;
+    };
+    __device__ __forceinline__ Inc inc(const T* d) const {
+        Inc q;
+        q.r1i = T(1) / (r0 + d[0]);
+        q.du = (d[1] - u0 * d[0]) * q.r1i;
+        q.dv = (d[2] - v0 * d[0]) * q.r1i;
+        q.m1 = m0 + d[1];
+        q.n1 = n0 + d[2];
+        q.dmu = fma(d[1], u0, q.m1 * q.du);
+        q.dnv = fma(d[2], v0, q.n1 * q.dv);
+        q.dp = gm1 * (d[3] - T(0.5) * (q.dmu + q.dnv));
+        return q;
+    }
+    // deviations of both fluxes at a state of deviation d
+    __device__ __forceinline__ void flux2(const T* d, T* fx, T* fy) const {
+        const Inc q = inc(d);
+        const T dep = d[3] + q.dp;
+        const T ep1 = ep0 + dep;
+        fx[0] = d[1];
+        fx[1] = q.dmu + q.dp;
+        fx[2] = fma(d[2], u0, q.n1 * q.du);
+        fx[3] = fma(dep, u0, ep1 * q.du);
+        fy[0] = d[2];
+        fy[1] = fma(d[1], v0, q.m1 * q.dv);
+        fy[2] = q.dnv + q.dp;
+        fy[3] = fma(dep, v0, ep1 * q.dv);
+    }
+    // deviation of the normal flux along +e_AXIS and the full state's wave
+    // speed |v_n| + c
+    template <int AXIS>
+    __device__ __forceinline__ T fluxn(const T* d, T* f) const {
+        const Inc q = inc(d);
+        const T dep = d[3] + q.dp;
+        const T ep1 = ep0 + dep;
+        if (AXIS == 0) {
+            f[0] = d[1];
+            f[1] = q.dmu + q.dp;
+            f[2] = fma(d[2], u0, q.n1 * q.du);
+            f[3] = fma(dep, u0, ep1 * q.du);
+        } else {
+            f[0] = d[2];
+            f[1] = fma(d[1], v0, q.m1 * q.dv);
+            f[2] = q.dnv + q.dp;
+            f[3] = fma(dep, v0, ep1 * q.dv);
+        }
+        const T vn = AXIS == 0 ? u0 + q.du : v0 + q.dv;
+        const T c2 = gamma * (p0 + q.dp) * q.r1i;
+        return fabs(vn) + sqrt(c2 > T(0) ? c2 : T(0));
+    }
+};
+
 // Lax--Friedrichs flux through a face with normal +e_AXIS from the state on
 // the low side uL to the state on the high side uR; alpha is local to the
 // point: max of |f'.nu| over both traces.
@@ -159,6 +249,28 @@ __device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const 
     const T al = sL > sR ? sL : sR;
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+}
+
+// The same flux in deviation form: uL, uR and F are deviations from the
+// base of ph (F = fhat - f(c).nu; the jump uR - uL is the same).
+template <class T, int AXIS>
+__device__ __forceinline__ void llf(const EulerDev<T>& ph, const T* uL, const T* uR, T* F) {
+    T fL[4], fR[4];
+    const T sL = ph.template fluxn<AXIS>(uL, fL);
+    const T sR = ph.template fluxn<AXIS>(uR, fR);
+    const T al = sL > sR ? sL : sR;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+}
+
+// llf for either kind of flux object (physical fluxes or deviation form)
+template <int AXIS, class T, int PHYS>
+__device__ __forceinline__ void llf_ax(const Phys<T, PHYS>& ph, const T* uL, const T* uR, T* F) {
+    llf<T, PHYS, AXIS>(ph, uL, uR, F);
+}
+template <int AXIS, class T>
+__device__ __forceinline__ void llf_ax(const EulerDev<T>& ph, const T* uL, const T* uR, T* F) {
+    llf<T, AXIS>(ph, uL, uR, F);
 }
 
 // The Lax--Friedrichs flux of llf from states whose normal fluxes and wave

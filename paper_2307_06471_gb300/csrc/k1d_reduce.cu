@@ -102,7 +102,7 @@ cudaError_t info_step1d(int phys, int prec, int k, int s, KernelInfo* info) {
 cudaError_t launch_reduce(int dim, int phys, int prec, const void* u, int nx, int ny, int nm, double dx, double dy,
                           double gamma, double bx, double by, DevState* ds, double* partials, int blocks, int set_dt,
                           cudaStream_t st) {
-    if (prec == 2) return reduce_euler_f32c(u, nx, ny, nm, dx, dy, gamma, ds, partials, blocks, set_dt, st);
+    if (prec == 2 || prec == 3) return reduce_euler_f32c(u, nx, ny, nm, dx, dy, gamma, ds, partials, blocks, set_dt, st);
 #define CRK_R(T, P, NV) reduce_t<T, P, NV>(u, nx, ny, nm, dx, dy, gamma, bx, by, ds, partials, blocks, set_dt, st)
     if (phys == PHYS_ADV) return prec == 0 ? CRK_R(float, PHYS_ADV, 1) : CRK_R(double, PHYS_ADV, 1);
     if (dim == 1) return prec == 0 ? CRK_R(float, PHYS_EULER1D, 3) : CRK_R(double, PHYS_EULER1D, 3);
@@ -117,7 +117,7 @@ cudaError_t launch_project(int dim, int phys, int prec, int k, int basis, const 
             return prec == 0 ? project1d_k<float, 1>(k, vals, u, ncell, st) : project1d_k<double, 1>(k, vals, u, ncell, st);
         return prec == 0 ? project1d_k<float, 3>(k, vals, u, ncell, st) : project1d_k<double, 3>(k, vals, u, ncell, st);
     }
-    if (prec == 2) return project2d_euler_f32c(k, basis, vals, u, ncell, st);
+    if (prec == 2 || prec == 3) return project2d_euler_f32c(k, basis, vals, u, ncell, st);
     if (phys == PHYS_EULER)
         return prec == 0 ? project2d_euler_f32(k, basis, vals, u, ncell, st)
                          : project2d_euler_f64(k, basis, vals, u, ncell, st);
@@ -126,7 +126,7 @@ cudaError_t launch_project(int dim, int phys, int prec, int k, int basis, const 
 
 cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,
                          cudaStream_t st) {
-    const int blocks = 4 * 152;
+    const int blocks = 4 * std::max(1, sm_count());
     if (prec == 1)
         axpby_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double*>(out), static_cast<const double*>(x),
                                                      static_cast<const double*>(y), alpha, beta, n);
@@ -156,12 +156,12 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restri
 }  // namespace
 
 cudaError_t launch_f64_to_f32(const double* in, float* out, size_t n, int comp, cudaStream_t st) {
-    f64_to_f32_kernel<<<8 * 152, 256, 0, st>>>(in, out, n, comp);
+    f64_to_f32_kernel<<<8 * std::max(1, sm_count()), 256, 0, st>>>(in, out, n, comp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_f32_to_f64(const float* in, double* out, size_t n, int comp, cudaStream_t st) {
-    f32_to_f64_kernel<<<8 * 152, 256, 0, st>>>(in, out, n, comp);
+    f32_to_f64_kernel<<<8 * std::max(1, sm_count()), 256, 0, st>>>(in, out, n, comp);
     return cudaGetLastError();
 }
 
@@ -172,6 +172,7 @@ cudaError_t launch_set_time(DevState* ds, double t, cudaStream_t st) {
 
 cudaError_t launch_step2d(int phys, int prec, int k, int basis, const StepArgs& a, int wpb, cudaStream_t st) {
     if (prec == 2) return step2d_euler_f32c(k, basis, a, wpb, st);
+    if (prec == 3) return step2d_euler_f32d(k, basis, a, wpb, st);
     if (phys == PHYS_EULER)
         return prec == 0 ? step2d_euler_f32(k, basis, a, wpb, st) : step2d_euler_f64(k, basis, a, wpb, st);
     return prec == 0 ? step2d_adv_f32(k, basis, a, wpb, st) : step2d_adv_f64(k, basis, a, wpb, st);
@@ -179,6 +180,7 @@ cudaError_t launch_step2d(int phys, int prec, int k, int basis, const StepArgs& 
 
 cudaError_t info_step2d(int phys, int prec, int k, int basis, int s, KernelInfo* info) {
     if (prec == 2) return info2d_euler_f32c(k, basis, s, info);
+    if (prec == 3) return info2d_euler_f32d(k, basis, s, info);
     if (phys == PHYS_EULER)
         return prec == 0 ? info2d_euler_f32(k, basis, s, info) : info2d_euler_f64(k, basis, s, info);
     return prec == 0 ? info2d_adv_f32(k, basis, s, info) : info2d_adv_f64(k, basis, s, info);

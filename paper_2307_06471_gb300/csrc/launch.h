@@ -3,9 +3,25 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace crk {
+
+// Streaming multiprocessors of the current device (queried once per device
+// ordinal; 0 if the query fails).
+inline int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
 
 struct KernelInfo {
     int regs;              // registers per thread of the step kernel
@@ -44,6 +60,10 @@ cudaError_t info2d_euler_f32c(int k, int basis, int s, KernelInfo* info);
 cudaError_t project2d_euler_f32c(int k, int basis, const double* vals, void* u, int ncell, cudaStream_t st);
 cudaError_t reduce_euler_f32c(const void* u, int nx, int ny, int nm, double dx, double dy, double gamma, DevState* ds,
                               double* partials, int blocks, int set_dt, cudaStream_t st);
+
+// compensated FP32 state with deviation-form fluxes (same planes as f32c)
+cudaError_t step2d_euler_f32d(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t info2d_euler_f32d(int k, int basis, int s, KernelInfo* info);
 
 // FP32 2D Euler k = 2 step with the fused learned indicator
 cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);

@@ -32,9 +32,12 @@ struct NoAllocScratch {
 // about 64 KiB, held by every GPU that loads the library until the process exits
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Device address of the array, looked up once per device.  In host code the
-// symbol name is only a host-side stand-in; the address must come from
-// cudaGetSymbolAddress with that device current.
+// Device address of the array.  In host code the symbol name is only a
+// host-side stand-in; the address must come from cudaGetSymbolAddress with
+// that device current.  It is looked up again at every call made outside a
+// stream capture (so a context that was reset and recreated gets its own
+// array's address, not a stale one); a call made while its stream is being
+// captured uses the address the last uncaptured call on that device found.
 constexpr int kMaxDevices = 64;
 NoAllocScratch* g_addr[kMaxDevices] = {nullptr};
 std::mutex g_mtx;
@@ -45,10 +48,13 @@ int fail(int code, const std::string& m) {
     return code;
 }
 
+// results of the reduction and its status bits, which the next call's
+// clearing would otherwise erase
 __global__ void copy_results(const crk::DevState* ds, int nv, double* out) {
     if (threadIdx.x == 0) {
         out[0] = ds->maxspeed;
         for (int v = 0; v < nv; ++v) out[1 + v] = ds->sums[v];
+        out[1 + nv] = double(ds->status);
     }
 }
 
@@ -61,7 +67,11 @@ extern "C" int crkdg_reduce_state_noalloc(const void* u_dev, int dim, int nx, in
                                           double* out_dev, void* stream) {
     if (!u_dev || !out_dev) return fail(CRKDG_EINVAL, "null state or output pointer");
     if (dim != 1 && dim != 2) return fail(CRKDG_EINVAL, "dim must be 1 or 2");
-    if (dim == 1) ny = 1;
+    // a 1D mesh is one row of cells of unit height (as crkdg_create makes it)
+    if (dim == 1) {
+        ny = 1;
+        dy = 1.0;
+    }
     if (nx < 1 || ny < 1 || n_modes < 1) return fail(CRKDG_EINVAL, "mesh and modes must be positive");
     if ((long long)nx * ny > kMaxCells)
         return fail(CRKDG_EINVAL, "mesh exceeds the 2^30-cell maximum of crkdg_reduce_state_noalloc");
@@ -74,19 +84,26 @@ extern "C" int crkdg_reduce_state_noalloc(const void* u_dev, int dim, int nx, in
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(CRKDG_ECUDA, "no usable current device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();   // a query refused during another stream's capture: treat as capturing
+        cap = cudaStreamCaptureStatusActive;
+    }
     NoAllocScratch* s = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mtx);
-        if (!g_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p)
                 return fail(CRKDG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             g_addr[dev] = static_cast<NoAllocScratch*>(p);
+        } else if (!g_addr[dev]) {
+            return fail(CRKDG_EINVAL, "the first call on a device must come before any stream capture");
         }
         s = g_addr[dev];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: the counter and results
     // must start at zero
     cudaError_t e = cudaMemsetAsync(&s->ds, 0, sizeof(crk::DevState), st);

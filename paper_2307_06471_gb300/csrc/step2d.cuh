@@ -399,8 +399,20 @@ constexpr size_t mlp_smem_bytes(int nthr) {
 
 // LIM = false: an instantiation without the limit-on-load code, for steps
 // whose u^n needs no limiting here (none pending, or a separate pass did it).
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, class PV>
+// DEV = true (with COMP, 2D Euler, FP32): every state is held as its
+// deviation from the cell's base state (the high part of its average at t^n)
+// and every flux in deviation form (EulerDev), so that the stage operators
+// and the final stage carry FP32 errors relative to their own size; the
+// compensated state then accumulates increments that are accurate to a few
+// ulps of themselves.  Face traces and face fluxes that cross to a
+// neighbouring cell move to its base by the deviation of the base
+// difference.  Inner stages, final stage and the update all run on the FP32
+// pipe.
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false,
+          class PV>
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
+    static_assert(!DEV || (COMP && PHYS == PHYS_EULER && sizeof(T) == 4 && !MLPI && !LIM && !CRK_LF_REUSE),
+                  "the deviation form is built for the compensated FP32 2D Euler step without limiters");
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
     constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
@@ -458,7 +470,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     // launch constants: 1/dx, 1/dy and the limiter thresholds made on the host
     // (set_derived), no FP64 division per warp
     constexpr bool F32 = sizeof(T) == 4;
-    Phys<T, PHYS> ph;
+    std::conditional_t<DEV, EulerDev<T>, Phys<T, PHYS>> ph;
     if constexpr (PHYS == PHYS_EULER) {
         ph.gamma = T(a.gamma);
         ph.gm1 = T(a.gamma - 1.0);
@@ -538,6 +550,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         }
     };
     if (LIM && a.limit) load_avg(rstart - 1, avg_prev);
+    T cprev[NV];   // DEV: base state of the row below (the previous row of the march)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cprev[v] = T(0);
     const double hh_ = pv.dx() > pv.dy() ? pv.dx() : pv.dy();
     const double mlp_scale = a.M * hh_ * hh_;
 
@@ -555,6 +570,49 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         for (int v = 0; v < NV; ++v)
 #pragma unroll
             for (int m = 0; m < NM; ++m) un[v][m] = uin[(size_t)(v * NM + m) * plane + cidx];
+
+        // DEV: the base cb = hi part of the average; un becomes the deviation
+        // (lo of the average, hi + lo of the higher modes); dcE / dcW / dcS are
+        // the east / west / south neighbours' bases minus this cell's
+        T cb[NV], dcE[NV], dcW[NV], dcS[NV];
+        if constexpr (DEV) {
+            const size_t lo_off = (size_t)C::NDOF * plane;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                cb[v] = un[v][0];
+                un[v][0] = uin[lo_off + (size_t)(v * NM) * plane + cidx];
+#pragma unroll
+                for (int m = 1; m < NM; ++m) un[v][m] += uin[lo_off + (size_t)(v * NM + m) * plane + cidx];
+            }
+            ph.set_base(cb);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                dcE[v] = shfl_down(cb[v], 1) - cb[v];
+                dcW[v] = shfl_up(cb[v], 1) - cb[v];
+                dcS[v] = cprev[v] - cb[v];
+                cprev[v] = cb[v];
+            }
+        }
+        // exterior state at a boundary point from an interior trace (DEV:
+        // both as deviations from this cell's base; the affine sides exactly)
+        auto bcx = [&](const BCSide& bc, int axis, const T* din, auto&& xyt, T* out) {
+            if constexpr (DEV) {
+                if (bc.affine) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        out[v] = fma(T(bc.m[v]), din[v], fma(T(bc.m[v]) - T(1), cb[v], T(bc.cf[v])));
+                } else {
+                    T full[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) full[v] = cb[v] + din[v];
+                    bc_exterior<T, NV>(bc, axis, full, xyt, out);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) out[v] -= cb[v];
+                }
+            } else {
+                bc_exterior<T, NV>(bc, axis, din, xyt, out);
+            }
+        };
 
         if (LIM && a.limit) {
             T avg_cur[NV], nbW[NV], nbE[NV];
@@ -821,7 +879,10 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int p = 0; p < NQ; ++p)
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) tWn[p][v] = shfl_down(tW[p][v], 1);
+                    for (int v = 0; v < NV; ++v) {
+                        tWn[p][v] = shfl_down(tW[p][v], 1);
+                        if constexpr (DEV) tWn[p][v] += dcE[v];
+                    }
                 // boundary strips: the whole warp forms the exterior states (no
                 // divergent branch), only the lane at the boundary keeps them
                 if (has_bcW) {
@@ -832,7 +893,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         for (int p = 0; p < NQ; ++p)
 #pragma unroll
                             for (int v = 0; v < NV; ++v) {
-                                const T ext = fma(T(bcw.m[v]), tWn[p][v], sizeof(T) == 4 ? T(bcw.cf[v]) : T(bcw.cd[v]));
+                                T k0 = sizeof(T) == 4 ? T(bcw.cf[v]) : T(bcw.cd[v]);
+                                if constexpr (DEV) k0 = fma(T(bcw.m[v]) - T(1), cb[v], k0);
+                                const T ext = fma(T(bcw.m[v]), tWn[p][v], k0);
                                 tE[p][v] = edge ? ext : tE[p][v];
                             }
                     } else {
@@ -841,7 +904,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
-                            bc_exterior<T, NV>(bcw, 0, tWn[p], [&](double& x, double& y, double& t) {
+                            bcx(bcw, 0, tWn[p], [&](double& x, double& y, double& t) {
                                 x = pv.x0();
                                 y = pv.y0() + (ryc + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
                                 t = t0 + tab_c(a, ic) * dt;
@@ -859,7 +922,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         for (int p = 0; p < NQ; ++p)
 #pragma unroll
                             for (int v = 0; v < NV; ++v) {
-                                const T ext = fma(T(bce.m[v]), tE[p][v], sizeof(T) == 4 ? T(bce.cf[v]) : T(bce.cd[v]));
+                                T k0 = sizeof(T) == 4 ? T(bce.cf[v]) : T(bce.cd[v]);
+                                if constexpr (DEV) k0 = fma(T(bce.m[v]) - T(1), cb[v], k0);
+                                const T ext = fma(T(bce.m[v]), tE[p][v], k0);
                                 tWn[p][v] = edge ? ext : tWn[p][v];
                             }
                     } else {
@@ -868,7 +933,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                         for (int p = 0; p < NQ; ++p) {
                             T ext[NV];
-                            bc_exterior<T, NV>(bce, 0, tE[p], [&](double& x, double& y, double& t) {
+                            bcx(bce, 0, tE[p], [&](double& x, double& y, double& t) {
                                 x = pv.x0() + nx * pv.dx();
                                 y = pv.y0() + (ryc + 0.5 + 0.5 * tb.xq[p]) * pv.dy();
                                 t = t0 + tab_c(a, ic) * dt;
@@ -881,7 +946,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T F[NV];
-                    llf<T, PHYS, 0>(ph, tE[p], tWn[p], F);
+                    llf_ax<0>(ph, tE[p], tWn[p], F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FE[p][v] += bi * F[v];
                 }
@@ -894,7 +959,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     const int colc = opaque(col), ic = opaque(i);
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
-                        bc_exterior<T, NV>(a.bc[2], 1, tS[p], [&](double& x, double& y, double& t) {
+                        bcx(a.bc[2], 1, tS[p], [&](double& x, double& y, double& t) {
                             x = pv.x0() + (colc + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
                             y = pv.y0();
                             t = t0 + tab_c(a, ic) * dt;
@@ -903,12 +968,15 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                     for (int p = 0; p < NQ; ++p)
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) lo[p][v] = slot(offN + (i * NQ + p) * NV + v);
+                        for (int v = 0; v < NV; ++v) {
+                            lo[p][v] = slot(offN + (i * NQ + p) * NV + v);
+                            if constexpr (DEV) lo[p][v] += dcS[v];
+                        }
                 }
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T F[NV];
-                    llf<T, PHYS, 1>(ph, lo[p], tS[p], F);
+                    llf_ax<1>(ph, lo[p], tS[p], F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FS[p][v] += bi * F[v];
                 }
@@ -997,6 +1065,10 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             red_max = fmax(red_max, sp);
         };
         if (do_south && r - 1 >= r0 && r - 1 < r1) {
+            // DEV: FS is relative to this row's base; the row below takes it
+            // relative to its own: minus f_y(c_below) - f_y(c) (sum_i b_i = 1)
+            T gS[NV];
+            if constexpr (DEV) ph.template fluxn<1>(dcS, gS);
             T P[NV][NM];
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -1005,6 +1077,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     T s = T(0);
 #pragma unroll
                     for (int p = 0; p < NQ; ++p) s += FS[p][v] * T(tb.pN[p][m]);
+                    if constexpr (DEV) {
+                        if (tb.sN[m] != 0.0) s -= gS[v] * T(tb.sN[m]);
+                    }
                     P[v][m] = slot(offP + v * NM + m) - tdt * T(tb.cm[m]) * (ry * s);
                 }
             finish(P, r - 1);
@@ -1012,11 +1087,21 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         if (!out_row) continue;
 
         // ---- this row: east/west/south faces and the volume term ----------------------
+        // DEV: FE of the lane to the left is relative to its base; moved to this
+        // cell's: plus f_x(c_west) - f_x(c)
         T FW[NQ][NV];
 #pragma unroll
         for (int p = 0; p < NQ; ++p)
 #pragma unroll
             for (int v = 0; v < NV; ++v) FW[p][v] = shfl_up(FE[p][v], 1);
+        if constexpr (DEV) {
+            T gW[NV];
+            ph.template fluxn<0>(dcW, gW);
+#pragma unroll
+            for (int p = 0; p < NQ; ++p)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) FW[p][v] += gW[v];
+        }
         T P[NV][NM];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
@@ -1048,12 +1133,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     T lo[NV], hi[NV], F[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) lo[v] = slot(offN + (i * NQ + p) * NV + v);
-                    bc_exterior<T, NV>(a.bc[3], 1, lo, [&](double& x, double& y, double& t) {
+                    bcx(a.bc[3], 1, lo, [&](double& x, double& y, double& t) {
                         x = pv.x0() + (colc + 0.5) * pv.dx() + 0.5 * pv.dx() * tb.xq[p];
                         y = pv.y0() + ny * pv.dy();
                         t = ti;
                     }, hi);
-                    llf<T, PHYS, 1>(ph, lo, hi, F);
+                    llf_ax<1>(ph, lo, hi, F);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) FN[p][v] += bi * F[v];
                 }
@@ -1088,7 +1173,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true>
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false>
 __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MINB_ADV : CRK_STEP_MINB2)
     step2d_kernel(const StepArgs a) {
     if constexpr (MLPI) {
@@ -1101,7 +1186,7 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MIN
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
     const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};
-    step2d_body<T, K, B, PHYS, COMP, MLPI, LIM>(a, pv, gw);
+    step2d_body<T, K, B, PHYS, COMP, MLPI, LIM, DEV>(a, pv, gw);
 }
 
 // Batched ensemble: problems of different sizes and domains share the

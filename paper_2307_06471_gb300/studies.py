@@ -66,7 +66,7 @@ def vortex(sizes=(80, 160, 320), T=10.0, precision="f32", cfl=0.1):
     from paper_2307_06471_gb300 import build
     from paper_2307_06471_gb300 import tableaux as GTB
     build.build()
-    P = {"f32": B.F32, "f64": B.F64, "f32c": B.F32C}[precision]
+    P = {"f32": B.F32, "f64": B.F64, "f32c": B.F32C, "f32d": B.F32D}[precision]
     stream = torch.cuda.Stream()
     rows = []
     for N in sizes:

@@ -87,8 +87,9 @@ def make_pair_2d(nx, ny, box, k, basis, physics, tab, bcs, precision, gamma=1.4,
     codes = [gpu_bc(bcs[s]) for s in sides]
     mesh = B.make_mesh(2, nx, ny, box, [c[0] for c in codes], [c[1] for c in codes], [c[2] for c in codes])
     phys_id = B.EULER if physics == "euler" else B.ADVECTION
-    solver = B.Solver(mesh, k, B.BASIS_P if basis == "P" else B.BASIS_Q, GTB.BY_NAME[tab], phys_id,
-                      B.F64 if precision == "f64" else B.F32, gamma=gamma, beta=beta)
+    prec = {"f64": B.F64, "f32": B.F32, "f32c": B.F32C, "f32d": B.F32D}[precision]
+    solver = B.Solver(mesh, k, B.BASIS_P if basis == "P" else B.BASIS_Q, GTB.BY_NAME[tab], phys_id, prec,
+                      gamma=gamma, beta=beta)
     ph = Euler(gamma, 2) if physics == "euler" else Advection(list(beta))
     obc = {s: oracle_bc(bcs[s], 0 if s in ("W", "E") else 1) for s in sides}
     dg = DG2D(nx, ny, box, k, basis, ph, obc)
@@ -121,5 +122,18 @@ def make_pair_1d(nx, box, k, physics, tab, bcs, precision, gamma=1.4, beta=1.0):
     return solver, dg
 
 
-def rel_err(a, b):
-    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+def rel_err(a, b, vaxis=-2):
+    """Largest error relative to the scale of its own variable: max over the
+    conserved variables v of max|a_v - b_v| / s_v, with s_v = max|b_v| over
+    all cells and modes (the oracle layout [..., v, m] has v at axis -2; pass
+    vaxis=0 for library planes [v, m, y, x]).  A variable whose own scale is
+    below 1 % of max(1, max|b|) -- a component that is zero in the reference,
+    such as the momentum of a state at rest -- is measured against that
+    floor instead.  Each variable is held to its own size, so the largest
+    variable (the energy of a strong shock, hundreds of times the density)
+    cannot hide an error in a small one."""
+    a = np.moveaxis(np.asarray(a, dtype=np.float64), vaxis, 0)
+    b = np.moveaxis(np.asarray(b, dtype=np.float64), vaxis, 0)
+    floor = 1e-2 * max(1.0, float(np.max(np.abs(b))))
+    return max(float(np.max(np.abs(a[v] - b[v]))) / max(float(np.max(np.abs(b[v]))), floor)
+               for v in range(b.shape[0]))

@@ -34,9 +34,45 @@ def _bcs():
             "N": ("dmr_top", post, pre, st["x0"], st["slope"], st["xspeed"])}
 
 
-def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10):
+def _tvb_margin(dg, u, t, M, cells):
+    """Smallest distance of a TVB-minmod decision of the listed patch cells
+    from a tie, relative to the size of the compared numbers.  Per cell,
+    direction and characteristic field (the oracle's reading: a1 the slope
+    mode, a2/a3 the forward/backward average differences, projected with the
+    left eigenvectors at the cell average) the decision flips where
+    |a1| = M h^2 (the TVB threshold) or, above it, where |a1| equals the
+    smaller of |a2|, |a3| with all signs equal (minmod returns a1 itself:
+    not troubled, else troubled).  Each distance is divided by the largest
+    magnitude entering it, the sum of |L_fj| |u_j| over the projected
+    vector."""
+    from oracle.limiter import neighbour_averages
+    avg = u[..., 0]
+    nb = neighbour_averages(dg, avg, t)
+    best = np.inf
+    for (cy, cx) in cells:
+        ab = avg[cy, cx]
+        for axis, (m, hi, lo, h) in enumerate(((1, "E", "W", dg.dx), (2, "N", "S", dg.dy))):
+            L = np.linalg.inv(dg.phys.right_eigenvectors(ab, axis))
+            vecs = (u[cy, cx, :, m], nb[hi][cy, cx] - ab, ab - nb[lo][cy, cx])
+            a = [L @ v for v in vecs]
+            scale = [np.abs(L) @ np.abs(v) for v in vecs]
+            thr = M * h * h
+            for f in range(4):
+                best = min(best, abs(abs(a[0][f]) - thr) / max(thr, scale[0][f], 1e-300))
+                same = np.sign(a[1][f]) == np.sign(a[0][f]) == np.sign(a[2][f])
+                if abs(a[0][f]) > thr and same:
+                    other = min(abs(a[1][f]), abs(a[2][f]))
+                    sc = max(scale[0][f], scale[1][f], scale[2][f], 1e-300)
+                    best = min(best, abs(abs(a[0][f]) - other) / sc)
+    return best
+
+
+def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10, margins=False):
     """u: full state [y, x, v, m] (FP64 values of the GPU input); returns the
-    oracle's limited u^{n+1} of cell (y, x)."""
+    oracle's limited u^{n+1} of cell (y, x) and, with margins, the tie
+    margin (_tvb_margin) of every limiter decision the cell depends on: the
+    limit of u^n in the cell and its four neighbours, and the limit of
+    u^{n+1} in the cell."""
     dx, dy = (BOX[1] - BOX[0]) / NX, (BOX[3] - BOX[2]) / NY
     ya, yb = max(0, y - 3), min(NY, y + 4)
     xa, xb = max(0, x - 3), min(NX, x + 4)
@@ -48,7 +84,15 @@ def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10):
     lim = lambda v, t: positivity_limit(dg, tvb_limit(dg, v, M, t)[0], eps)
     p = u[ya:yb, xa:xb]
     w = crkdg_step(dg, lim(p, t0), t0, dt, OTB.SSPRK3, limiter=lim)
-    return w[y - ya, x - xa]
+    if not margins:
+        return w[y - ya, x - xa]
+    cy, cx = y - ya, x - xa
+    near = [(cy + j, cx + i) for (j, i) in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1))
+            if 0 <= cy + j < yb - ya and 0 <= cx + i < xb - xa]
+    m_n = _tvb_margin(dg, p, t0, M, near)
+    w_raw = crkdg_step(dg, lim(p, t0), t0, dt, OTB.SSPRK3)
+    m_n1 = _tvb_margin(dg, w_raw, t0 + dt, M, [(cy, cx)])
+    return w[y - ya, x - xa], min(m_n, m_n1)
 
 
 def _samples(rng, n_interior):
@@ -92,16 +136,23 @@ def test_full_size_dmr_sampled_cells(prec):
     code, status = s.sync()
     assert code == 0 and status == 0
     u = np.transpose(u_raw, (2, 3, 0, 1))
+    # each variable is measured against its own size over the domain (the
+    # energy behind the Mach 10 shock is ~25x the density)
+    scale = np.maximum(np.max(np.abs(u[..., 0]), axis=(0, 1)), 1e-2 * np.max(np.abs(u[..., 0])))
     rng = np.random.default_rng(2024)
     bad = []
     for (y, x) in _samples(rng, 24):
         want = _oracle_cell(u, y, x, t0, t1 - t0)
-        err = np.max(np.abs(got[y, x] - want)) / max(1.0, np.max(np.abs(want)))
+        err = np.max(np.max(np.abs(got[y, x] - want), axis=-1) / scale)
         tol = 1e-12 if prec == "f64" else 2e-5
         if not err < tol:
             bad.append((y, x, err))
     if prec == "f64":
         assert not bad, bad
     else:
-        # FP32 limiter decisions may differ from FP64 ones at exact ties only
-        assert len(bad) <= 1, bad
+        # an FP32 result may leave the band only where a limiter decision it
+        # depends on sits within FP32 rounding of a tie: there either side of
+        # the tie is a correct result of the method
+        for (y, x, err) in bad:
+            _, margin = _oracle_cell(u, y, x, t0, t1 - t0, margins=True)
+            assert margin < 1e-4, (y, x, err, margin)

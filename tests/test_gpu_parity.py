@@ -505,8 +505,8 @@ def test_compensated_state_tracks_fp64_over_many_steps():
             s.step(2e-4)
         res[name] = (s.get_state(), np.abs(s.conservation() - m0) / np.abs(m0))
         s.close()
-    e32 = rel_err(res["f32"][0], res["f64"][0])
-    e32c = rel_err(res["f32c"][0], res["f64"][0])
+    e32 = rel_err(res["f32"][0], res["f64"][0], vaxis=0)
+    e32c = rel_err(res["f32c"][0], res["f64"][0], vaxis=0)
     assert e32c < 1e-6
     assert e32c < 0.2 * e32
     assert np.max(res["f32c"][1]) < 0.5 * np.max(res["f32"][1])
