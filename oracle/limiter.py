@@ -84,30 +84,29 @@ def tvb_limit(dg, u, M, t, force=None):
     u = np.array(u, dtype=np.float64, copy=True)
     if dg.B.nm < 3:
         return u, np.zeros((dg.ny, dg.nx), dtype=bool)
-    avg = u[..., 0]
+    avg = u[..., 0]                                   # [y, x, v]
     nb = neighbour_averages(dg, avg, t)
     systems = isinstance(dg.phys, Euler)
-    flags = np.zeros((dg.ny, dg.nx), dtype=bool)
-    newx = np.empty_like(u[..., 1])
-    newy = np.empty_like(u[..., 2])
-    for y in range(dg.ny):
-        for x in range(dg.nx):
-            ab = avg[y, x]
-            ax = (u[y, x, :, 1], nb["E"][y, x] - ab, ab - nb["W"][y, x])
-            ay = (u[y, x, :, 2], nb["N"][y, x] - ab, ab - nb["S"][y, x])
-            if systems:
-                Rx = dg.phys.right_eigenvectors(ab, 0)
-                Ry = dg.phys.right_eigenvectors(ab, 1)
-                Lx, Ly = np.linalg.inv(Rx), np.linalg.inv(Ry)
-                cx = [Lx @ a for a in ax]
-                cy = [Ly @ a for a in ay]
-            else:
-                cx, cy = list(ax), list(ay)
-            mx = tvb_minmod(cx[0], cx[1], cx[2], M * dg.dx * dg.dx)
-            my = tvb_minmod(cy[0], cy[1], cy[2], M * dg.dy * dg.dy)
-            flags[y, x] = bool(np.any(mx != cx[0]) or np.any(my != cy[0])) if force is None else bool(force[y, x])
-            newx[y, x] = Rx @ mx if systems else mx
-            newy[y, x] = Ry @ my if systems else my
+    # every cell at once; per cell and direction: (a1, a2, a3) as above
+    ax = (u[..., :, 1], nb["E"] - avg, avg - nb["W"])
+    ay = (u[..., :, 2], nb["N"] - avg, avg - nb["S"])
+    mv = lambda A, a: np.einsum("yxij,yxj->yxi", A, a)    # per-cell matrix times vector
+    if systems:
+        Rx = dg.phys.right_eigenvectors(avg, 0)           # [y, x, 4, 4]
+        Ry = dg.phys.right_eigenvectors(avg, 1)
+        Lx, Ly = np.linalg.inv(Rx), np.linalg.inv(Ry)
+        cx = [mv(Lx, a) for a in ax]
+        cy = [mv(Ly, a) for a in ay]
+    else:
+        cx, cy = list(ax), list(ay)
+    mx = tvb_minmod(cx[0], cx[1], cx[2], M * dg.dx * dg.dx)
+    my = tvb_minmod(cy[0], cy[1], cy[2], M * dg.dy * dg.dy)
+    if force is None:
+        flags = np.any(mx != cx[0], axis=-1) | np.any(my != cy[0], axis=-1)
+    else:
+        flags = np.asarray(force, dtype=bool).copy()
+    newx = mv(Rx, mx) if systems else mx
+    newy = mv(Ry, my) if systems else my
     out = u.copy()
     f = flags
     out[f, :, 1] = newx[f]

@@ -97,26 +97,28 @@ class Euler:
         return np.stack(comps, axis=-1)
 
     def right_eigenvectors(self, u, axis):
-        """Columns = right eigenvectors of d f_axis / d u at state u (one state,
-        2D only), for the eigenvalues (vn - c, vn, vn, vn + c).  Standard
-        scaling: first component 1 for the acoustic and entropy waves."""
+        """Columns = right eigenvectors of d f_axis / d u at the state u (2D
+        only), for the eigenvalues (vn - c, vn, vn, vn + c).  Standard
+        scaling: first component 1 for the acoustic and entropy waves.
+        u[..., 4] -> R[..., 4, 4] (one matrix per state)."""
         assert self.dim == 2
         rho, vel, p = self.primitive(u)
         w, v = vel
         c = np.sqrt(self.gamma * p / rho)
         H = (u[..., -1] + p) / rho
         q2 = w * w + v * v
+        one, zero = np.ones_like(w), np.zeros_like(w)
         if axis == 0:
-            R = np.array([[1.0, 1.0, 0.0, 1.0],
-                          [w - c, w, 0.0, w + c],
-                          [v, v, 1.0, v],
-                          [H - w * c, 0.5 * q2, v, H + w * c]])
+            rows = [[one, one, zero, one],
+                    [w - c, w, zero, w + c],
+                    [v, v, one, v],
+                    [H - w * c, 0.5 * q2, v, H + w * c]]
         else:
-            R = np.array([[1.0, 1.0, 0.0, 1.0],
-                          [w, w, 1.0, w],
-                          [v - c, v, 0.0, v + c],
-                          [H - v * c, 0.5 * q2, w, H + v * c]])
-        return R
+            rows = [[one, one, zero, one],
+                    [w, w, one, w],
+                    [v - c, v, zero, v + c],
+                    [H - v * c, 0.5 * q2, w, H + v * c]]
+        return np.stack([np.stack(r, axis=-1) for r in rows], axis=-2)
 
 
 def lf_flux(phys, uint, uext, axis, sign):
