@@ -22,6 +22,18 @@ e2e    : the same metric through the C ABI with host buffers, wall clock:
          device-driven steps (dt from each step's own reduction) with each
          step's run state (t, dt, max wave speed) read back asynchronously
          into pinned memory, download of the FP64 state into pinned memory.
+roofline : the fused step kernel (with its finalize) against the FP32 FMA
+         peak measured on this GPU by the library's probe (alu_peaks: FP32,
+         packed FP32x2 and FP64 FMA rates), HBM GB/s as context.
+fp64_arm : the same DMR workload with the FP64 state (CRKDG_F64), device
+         timed the same way over --fp64-steps steps.
+matched_l1 : the isentropic vortex (Q^2, RK4, CFL 0.1, T = --matched-T) in
+         FP64 on 80/120/160/240/320^2 and, on 80/160/320^2, in FP32, the
+         compensated FP32 state and
+         the deviation-form FP32 step (CRKDG_F32D) on the same meshes; each
+         FP32 run matched to the FP64 run of at most its density L1 error;
+         speedup = FP64 wall time / FP32 wall time (host clock, synchronised
+         device-driven runs).
 --impl reference : the FP64 CPU oracle (numpy) on a bounded sample of the
          same workload (a 240 x 60 mesh of the same problem), timed on the
          host cores; rank 0 only.
@@ -188,9 +200,10 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def oracle_sample(nx, ny, steps, warm=1):
-    """Run the FP64 oracle on the bounded sample in a single-threaded child
-    process; returns (DOF-updates/s, seconds, steps)."""
+def oracle_sample(nx, ny, steps, warm=1, procs=1):
+    """Run the FP64 oracle on the bounded sample in `procs` single-threaded
+    child processes at once; returns (aggregate DOF-updates/s, seconds of
+    the slowest copy, steps per copy)."""
     code = r"""
 import json, sys, time, os
 sys.path.insert(0, %r)
@@ -224,11 +237,19 @@ print(json.dumps({'sec': el, 'steps': steps, 'dofs': nx * ny * 24}))
 """ % (ROOT, nx, ny, steps, warm)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["dofs"] * d["steps"] / d["sec"], d["sec"], d["steps"]
+    # procs single-threaded copies at once, one per host core: the sample's
+    # steps are independent of each other's, so the aggregate is
+    # procs * DOF * steps over the slowest copy's time
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    res = []
+    for pr in ps:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    sec = max(d["sec"] for d in res)
+    return procs * res[0]["dofs"] * res[0]["steps"] / sec, sec, res[0]["steps"]
 
 
 def cpu_model():
@@ -278,20 +299,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     steps = max(1, args.steps)
-    # bound the run to a few minutes: ~1.3 s per oracle step at 240 x 60
+    # bound the run to a few minutes: ~0.3 s per oracle step at 240 x 60
     nx, ny = SAMPLE["nx"], SAMPLE["ny"]
-    if steps > 60:
+    if steps > 300:
         nx, ny = 120, 30
-    rate, sec, n = oracle_sample(nx, ny, steps, warm=max(1, min(args.warmup, 3)))
+    ncores = os.cpu_count() or 1
+    rate, sec, n = oracle_sample(nx, ny, steps, warm=max(1, min(args.warmup, 3)), procs=ncores)
     line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec / n, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WL["name"], "sample_mesh": "%dx%d" % (nx, ny), "k": 2, "basis": "P",
                        "tableau": "ssprk3", "limiter": "tvb M=50"},
             "impl": "reference",
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB, %d steps, 1 thread (%s)"
-                                       % (nx, ny, n, cpu_model())},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                             "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB + positivity, %d steps in "
+                                       "each of %d single-threaded copies run at once (one per host core), "
+                                       "aggregate rate; %s" % (nx, ny, n, ncores, cpu_model())},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line, default=float))
     return 0
@@ -308,6 +331,8 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm of the same workload")
     ap.add_argument("--fp64-steps", type=int, default=50)
+    ap.add_argument("--no-matched-l1", action="store_true", help="skip the vortex comparison at matched L1")
+    ap.add_argument("--matched-T", type=float, default=1.0)
     ap.add_argument("--limit-mode", default="pass", choices=["pass", "fused"],
                     help="pending limiter as a separate pass before the step kernel, or fused into its load")
     args = ap.parse_args()
@@ -427,12 +452,28 @@ def main():
                             "arithmetic (GB300's FP64 FMA rate is the f64 entry of alu_peaks)"}
         s64.close()
 
+    # the headline comparison at matched L1 error: the isentropic vortex (the
+    # paper-style exact-solution test, Q^2 RK4) to a short T in FP64 and in the
+    # FP32 variants, each FP32 run matched to the FP64 run of equal or lower
+    # error (same mesh within 10 %, else the coarsest FP64 mesh that reaches it)
+    matched = None
+    if rank == 0 and ws == 1 and not args.no_matched_l1:
+        from paper_2307_06471_gb300 import studies
+        matched = studies.matched_l1(T=args.matched_T)
+        # the same precisions' step rates on a mesh that fills the GPU (the
+        # 320^2 vortex holds ~3 warps per SM, so its rates are latency bound)
+        matched["rates_full_gpu"] = studies.precision_rates()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, sec, n = oracle_sample(SAMPLE["nx"], SAMPLE["ny"], 8)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB, %d steps (%.1f s), 1 thread, %s"
-                         % (SAMPLE["nx"], SAMPLE["ny"], n, sec, cpu_model())}
+        ncores = os.cpu_count() or 1
+        rate1, sec1, n1 = oracle_sample(SAMPLE["nx"], SAMPLE["ny"], 30)
+        rate, sec, n = oracle_sample(SAMPLE["nx"], SAMPLE["ny"], 10, procs=ncores)
+        cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+               "sample": "FP64 numpy oracle, DMR %dx%d P2 SSP-RK3 + TVB + positivity, %d steps in each of %d "
+                         "single-threaded copies run at once (one per host core; %.1f s), aggregate rate; %s"
+                         % (SAMPLE["nx"], SAMPLE["ny"], n, ncores, sec, cpu_model()),
+               "single_thread": {"value": rate1, "cores": 1, "steps": n1, "sec": sec1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -454,7 +495,7 @@ def main():
                                           % alu["sms"],
                              "flop_per_cell": fpc, "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / peaks["hbm_gbs"],
                              "hbm_peak_source": peak_kind},
-                "limit_pass": limit_pass, "alu_peaks": alu, "fp64_arm": fp64_arm,
+                "limit_pass": limit_pass, "alu_peaks": alu, "fp64_arm": fp64_arm, "matched_l1": matched,
                 "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps * (3 if use_pass else 2),
                 "status": {"code": code, "bits": status, "t_sim": t_sim},
                 "cpu_baseline": cpu}

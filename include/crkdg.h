@@ -226,6 +226,12 @@ int crkdg_sync(crkdg_ctx* ctx, unsigned* device_status);
 /* Current simulation time (host copy). */
 int crkdg_time(const crkdg_ctx* ctx, double* t);
 
+/* Number of 2D steps with dt > 0 the context has completed since its
+ * creation, counted by each step's device reduction (steps past t_end of a
+ * device-driven run, which leave the state unchanged, are not counted).
+ * Synchronises.  CRKDG_EUNSUPPORTED in 1D. */
+int crkdg_step_count(crkdg_ctx* ctx, unsigned long long* steps);
+
 /* Monitor a device-driven run without stalling it: enqueue on the context
  * stream a copy of the device run state into out[5] = {t, dt of the next
  * step, t_end, cfl, maximum wave speed (max_K (|u|+c)/dx + (|v|+c)/dy of the

@@ -73,6 +73,7 @@ _SIGS = {
     "crkdg_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "crkdg_set_limit_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "crkdg_run_state_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "crkdg_step_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
     "crkdg_apply_limit": (C.c_int, [C.c_void_p]),
     "crkdg_set_operator_form": (C.c_int, [C.c_void_p, C.c_int]),
     "crkdg_get_operator_form": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
@@ -295,6 +296,11 @@ class Solver:
         st = C.c_uint()
         code = lib().crkdg_sync(self.ctx, C.byref(st))
         return code, st.value
+
+    def step_count(self):
+        n = C.c_ulonglong()
+        _check(lib().crkdg_step_count(self.ctx, C.byref(n)))
+        return n.value
 
     def time(self):
         t = C.c_double()

@@ -894,6 +894,14 @@ int crkdg_time(const crkdg_ctx* cc, double* t) {
     return CRKDG_OK;
 }
 
+int crkdg_step_count(crkdg_ctx* c, unsigned long long* steps) {
+    if (check_ctx(c) || !steps) return fail(CRKDG_EINVAL, "null argument");
+    if (c->dim != 2) return fail(CRKDG_EUNSUPPORTED, "the step counter is kept by the 2D step");
+    CK(cudaMemcpyAsync(steps, &c->d_state->steps, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CRKDG_OK;
+}
+
 int crkdg_run_state_async(crkdg_ctx* c, double* out) {
     if (check_ctx(c) || !out) return fail(CRKDG_EINVAL, "null argument");
     static_assert(offsetof(DevState, maxspeed) == 4 * sizeof(double), "run state layout");

@@ -485,10 +485,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const bool do_tvb = a.tvb_on, do_pp = a.pp_on;
     const T pp_eps = F32 ? T(a.pp_epsf) : T(a.pp_eps);
 
-    // FP32 state: the per-cell wave speed and status tests of the epilogue run
-    // in FP32 (GB300's FP64 pipe is 1/64 of its FP32 rate), the column totals
-    // in compensated FP32 (TwoSum), converted to FP64 once per warp
-    constexpr bool F32R = sizeof(T) == 4 && !COMP;
+    // FP32 state (plain or compensated): the per-cell wave speed and status
+    // tests of the epilogue run in FP32 (GB300's FP64 pipe is 1/64 of its FP32
+    // rate), the column totals in compensated FP32 (TwoSum; a compensated
+    // state adds its lo parts into the error term), converted to FP64 once per
+    // warp
+    constexpr bool F32R = sizeof(T) == 4;
     T cs_hi[NV], cs_lo[NV];
     T red_maxT = T(0);
 #pragma unroll
@@ -995,16 +997,41 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             if (!outlane) return;
             const size_t o = (size_t)rw * nx + col;
             if constexpr (F32R) {
+                T avl[NV];   // COMP: lo part of the new averages
+                if constexpr (COMP) {
+                    // P holds Delta: u^{n+1} = (hi + lo) + Delta, hi' + lo' by
+                    // TwoSum; P[v][0] becomes hi' of the average
+                    const size_t lo_off = (size_t)C::NDOF * plane;
 #pragma unroll
-                for (int v = 0; v < NV; ++v)
+                    for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
+                        for (int m = 0; m < NM; ++m) {
+                            const size_t ix = (size_t)(v * NM + m) * plane + o;
+                            const T hi = uin[ix], lo = uin[lo_off + ix];
+                            const T d = P[v][m] + lo;
+                            const T sum = hi + d;
+                            const T bv = sum - hi;
+                            const T err = (hi - (sum - bv)) + (d - bv);
+                            uout[ix] = sum;
+                            uout[lo_off + ix] = err;
+                            if (m == 0) {
+                                P[v][0] = sum;
+                                avl[v] = err;
+                            }
+                        }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) uout[(size_t)(v * NM + m) * plane + o] = P[v][m];
+                }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {   // TwoSum: cs_hi + cs_lo += P[v][0] exactly
                     const T x = P[v][0];
                     const T sum = cs_hi[v] + x;
                     const T bv = sum - cs_hi[v];
                     cs_lo[v] += (cs_hi[v] - (sum - bv)) + (x - bv);
+                    if constexpr (COMP) cs_lo[v] += avl[v];
                     cs_hi[v] = sum;
                 }
                 if constexpr (PHYS == PHYS_EULER) {

@@ -59,6 +59,109 @@ def density_l1(state, k, basis, box, exact, nq=5):
     return float(np.sum(e * np.outer(w, w)) * 0.25 / (nx * ny))
 
 
+def vortex_run(N, T, precision, stream_handle, cfl=0.1, chunk=100):
+    """One isentropic-vortex run (Q^2, RK4, periodic [0,10]^2) to T with
+    device-driven steps (CUDA-graph replays of `chunk` steps): density L1 at
+    T against the exact translated vortex, wall time of the stepping (host
+    clock around the synchronised run), steps, DOF-updates/s, FP64 totals
+    drift, device status."""
+    import torch
+    import crkdg_inputs as inp
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    P = {"f32": B.F32, "f64": B.F64, "f32c": B.F32C, "f32d": B.F32D}[precision]
+    mesh = B.make_mesh(2, N, N, (0.0, 10.0, 0.0, 10.0), [B.BC_PERIODIC] * 4)
+    s = B.Solver(mesh, 2, B.BASIS_Q, GTB.RK4, B.EULER, P, stream=stream_handle)
+    s.project_function(lambda X, Y: inp.vortex_ic(X, Y))
+    m0 = s.conservation()
+    e0 = density_l1(s.get_state(), 2, "Q", (0, 10, 0, 10), lambda X, Y: inp.vortex_ic(X, Y))
+    n0 = s.step_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while True:
+        s.advance(chunk, cfl, T, capture=True)
+        if s.time() >= T * (1 - 1e-14):
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    steps = s.step_count() - n0
+    u = s.get_state()
+    err = density_l1(u, 2, "Q", (0, 10, 0, 10), lambda X, Y: inp.vortex_ic(X, Y, T))
+    m1 = s.conservation()
+    code, st = s.sync()
+    s.close()
+    return {"precision": precision, "N": N, "T": T, "L1_density": err, "L1_projection": e0, "wall_s": wall,
+            "steps": steps, "dof_updates_per_s": N * N * 36 * steps / wall,
+            "mass_drift_rel": float(abs(m1[0] - m0[0]) / m0[0]),
+            "energy_drift_rel": float(abs(m1[3] - m0[3]) / m0[3]), "status": st}
+
+
+def precision_rates(N=1280, steps=40, warmup=5, variants=("f32", "f32c", "f32d", "f64")):
+    """Device-timed step rate of the vortex configuration (Q^2, RK4,
+    periodic) on an N x N mesh that fills the GPU (1280^2: 59M DOF; the
+    state copies, 236 MB per FP32 plane set, exceed L2), per precision:
+    `steps` device-driven steps (dt from each step's own reduction) between
+    CUDA events on the solver's stream, after `warmup` steps."""
+    import torch
+    import crkdg_inputs as inp
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    stream = torch.cuda.Stream()
+    out = {}
+    for v in variants:
+        P = {"f32": B.F32, "f64": B.F64, "f32c": B.F32C, "f32d": B.F32D}[v]
+        mesh = B.make_mesh(2, N, N, (0.0, 10.0, 0.0, 10.0), [B.BC_PERIODIC] * 4)
+        s = B.Solver(mesh, 2, B.BASIS_Q, GTB.RK4, B.EULER, P, stream=stream.cuda_stream)
+        s.project_function(lambda X, Y: inp.vortex_ic(X, Y))
+        s.advance(warmup, 0.1, 10.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            s.step_device()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        code, st = s.sync()
+        out[v] = {"ms_per_step": ms, "dof_updates_per_s": N * N * 36 / (ms * 1e-3), "status": st}
+        s.close()
+    return {"workload": "isentropic vortex, Q2, RK4, %dx%d, %d device-driven steps" % (N, N, steps), "rates": out}
+
+
+def matched_l1(T=1.0, fp64_sizes=(80, 120, 160, 240, 320), fp32_sizes=(80, 160, 320),
+               variants=("f32", "f32c", "f32d")):
+    """Time to a given accuracy: the vortex to T in FP64 on fp64_sizes and in
+    each FP32 variant on fp32_sizes.  Each FP32 run is matched to an FP64 run
+    (the same mesh if its L1 is within 10 % of FP64's there, else the coarsest
+    FP64 mesh whose L1 is at most the FP32 run's); the speedup is that FP64
+    run's wall time over the FP32 run's.  Per variant the best matched run is
+    reported."""
+    import torch
+    stream = torch.cuda.Stream()
+    runs = [vortex_run(N, T, "f64", stream.cuda_stream) for N in fp64_sizes]
+    f64 = {r["N"]: r for r in runs}
+    best = {}
+    for v in variants:
+        for N in fp32_sizes:
+            r = vortex_run(N, T, v, stream.cuda_stream)
+            runs.append(r)
+            same = f64.get(N)
+            if same is not None and r["L1_density"] <= 1.1 * same["L1_density"]:
+                m = same
+            else:
+                ok = [f for f in sorted(f64.values(), key=lambda f: f["N"]) if f["L1_density"] <= r["L1_density"]]
+                m = ok[0] if ok else None
+            if m is None:
+                continue
+            rec = {"variant": v, "N": N, "L1": r["L1_density"], "wall_s": r["wall_s"],
+                   "fp64_N": m["N"], "fp64_L1": m["L1_density"], "fp64_wall_s": m["wall_s"],
+                   "speedup_vs_fp64": m["wall_s"] / r["wall_s"]}
+            if v not in best or rec["speedup_vs_fp64"] > best[v]["speedup_vs_fp64"]:
+                best[v] = rec
+    return {"workload": "isentropic vortex (strength 5, mean flow (1,1)), [0,10]^2 periodic, Q2, RK4, CFL 0.1, "
+                        "T=%g" % T, "runs": runs, "matched": best}
+
+
 def vortex(sizes=(80, 160, 320), T=10.0, precision="f32", cfl=0.1):
     import torch
     import crkdg_inputs as inp

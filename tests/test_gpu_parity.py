@@ -163,16 +163,18 @@ def _dmr_bcs():
             "N": ("dmr_top", post, pre, st["x0"], st["slope"], st["xspeed"])}, st
 
 
+@pytest.mark.parametrize("k,tab,cfl", [(2, "ssprk3", 0.16), (1, "ssprk3", 0.3), (1, "heun2", 0.3)])
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
-def test_dmr_boundaries_and_limiter(prec, tol):
-    """Double Mach reflection set-up: inflow W, outflow E, wall + post-shock
+def test_dmr_boundaries_and_limiter(prec, tol, k, tab, cfl):
+    """Double Mach reflection set-up (Sec. 4.2.2; P^2 at CFL 0.16 and P^1 at
+    CFL 0.3, the paper's CFL numbers): inflow W, outflow E, wall + post-shock
     S, exact shock motion N; TVB limiter M = 50 followed by the positivity
     scaling at the end of each step (applied on load by the next step, and by
     get_state)."""
     from oracle.limiter import positivity_limit
     bcs, st = _dmr_bcs()
     nx, ny = 64, 17
-    gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), 2, "P", "euler", "ssprk3", bcs, prec)
+    gs, dg = make_pair_2d(nx, ny, (0, 4, 0, 1), k, "P", "euler", tab, bcs, prec)
     gs.set_launch(seg_rows=6)
     X, Y = dg.volume_points()
     u = dg.project(lambda X, Y: inp.dmr_ic(X, Y, st))
@@ -185,9 +187,9 @@ def test_dmr_boundaries_and_limiter(prec, tol):
     w = lim(u, 0.0)
     t = 0.0
     for _ in range(3):
-        dt = gs.cfl_dt(0.16)
+        dt = gs.cfl_dt(cfl)
         gs.step(dt)
-        w = ocrkdg2(dg, w, t, dt, OTB.SSPRK3, limiter=lim)
+        w = ocrkdg2(dg, w, t, dt, TAB_NAMES[tab], limiter=lim)
         t += dt
     got = from_planes(gs.get_state())
     assert rel_err(got, w) < tol
