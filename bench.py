@@ -16,7 +16,9 @@ dt read on the device, and its one-block finalize (slot reduction, next dt).
 
 value  : DOF-updates/s = cells * 24 * K / (sum of per-step device times),
          CUDA events on the solver's stream around each step, L2 flushed
-         (256 MiB write) between timed steps, outside the events.
+         between timed steps, outside the events (256 MiB written, then
+         256 MiB of another buffer read, so the flush's own dirty lines are
+         written back before the events; --flush write: the write alone).
 e2e    : the same metric through the C ABI with host buffers, wall clock:
          upload of the FP64 initial state from pinned host memory, K
          device-driven steps (dt from each step's own reduction) with each
@@ -167,6 +169,31 @@ def alu_peaks(stream_handle):
     return out
 
 
+class L2Flush:
+    """Between timed steps: write a 256 MiB buffer (larger than the 126 MB
+    L2), then (mode "write+read", the default) read another 256 MiB buffer,
+    so that the write's dirty lines are written back during the flush and
+    not by the timed kernels that evict them."""
+
+    def __init__(self, mode):
+        import torch
+        n = 256 * 1024 * 1024 // 4
+        self.mode = mode
+        self.w = torch.empty(n, dtype=torch.float32, device="cuda")
+        self.r = torch.zeros(n, dtype=torch.float32, device="cuda") if mode == "write+read" else None
+        self.sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.w.zero_()
+        if self.r is not None:
+            self.sink.copy_(self.r.sum())
+
+    def describe(self):
+        return ("flushed between timed steps: 256 MiB written" +
+                (", then 256 MiB of another buffer read (the write-backs land in the flush)"
+                 if self.r is not None else ""))
+
+
 def timed_steps(s, stream, flush, steps, use_pass):
     """Device times (ms) of `steps` whole steps, each bracketed by CUDA events
     on the solver's stream, L2 flushed before each (outside the events):
@@ -178,7 +205,7 @@ def timed_steps(s, stream, flush, steps, use_pass):
     torch.cuda.synchronize()
     for i in range(steps):
         with torch.cuda.stream(stream):
-            flush.zero_()
+            flush()
         starts[i].record(stream)
         if use_pass:
             s.apply_limit()        # limiter pass of the previous step's final stage (in place)
@@ -332,6 +359,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 arm of the same workload")
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--no-matched-l1", action="store_true", help="skip the vortex comparison at matched L1")
+    ap.add_argument("--flush", default="write+read", choices=["write", "write+read"],
+                    help="L2 flush between timed steps (see L2Flush)")
     ap.add_argument("--matched-T", type=float, default=1.0)
     ap.add_argument("--limit-mode", default="pass", choices=["pass", "fused"],
                     help="pending limiter as a separate pass before the step kernel, or fused into its load")
@@ -363,7 +392,7 @@ def main():
     if args.autotune:
         s.autotune()
     seg_rows, wpb = s.get_launch()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(args.flush)
 
     # measured FP32 / FP64 FMA peaks (the roofline's denominator), before the
     # timed region
@@ -481,7 +510,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WL["name"], "cells": cells, "dof_per_cell": 24, "k": 2, "basis": "P",
                            "tableau": "ssprk3", "limiter": "tvb M=50 + positivity scaling (once per step)", "cfl": WL["cfl"],
-                           "reductions": "fp64", "l2": "flushed (256 MiB) between timed steps",
+                           "reductions": "fp64", "l2": flush.describe(),
                            "launch": {"seg_rows": seg_rows, "warps_per_block": wpb},
                            "limit_mode": "separate pass + fused step" if use_pass else "fused into the step's load",
                            "parallelism": "replicas" if ws > 1 else "single"},

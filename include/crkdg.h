@@ -262,7 +262,9 @@ int crkdg_autotune(crkdg_ctx* ctx, double* best_us);
  * differently in the two kernels); the pass costs one extra read of u^n but
  * spreads the limiter's uneven work (troubled cells gather at shocks) over
  * the whole GPU instead of the few warps that hold the shock.  The learned
- * indicator always runs fused.  EINVAL for another mode. */
+ * indicator (crkdg_set_indicator) follows the mode: evaluated in the pass
+ * (a grid of a few blocks per SM, each loading the weights once) or fused
+ * into the step's load.  EINVAL for another mode. */
 enum { CRKDG_LIMIT_FUSED = 0, CRKDG_LIMIT_PASS = 1 };
 int crkdg_set_limit_mode(crkdg_ctx* ctx, int mode);
 int crkdg_get_limit_mode(const crkdg_ctx* ctx, int* mode);

@@ -231,6 +231,14 @@ int enqueue_limit_pass(crkdg_ctx* c, double M, int dt_from_dev) {
     a.pp_eps = c->pp_pending;
     a.t = c->t;
     a.dt_from_dev = dt_from_dev;
+    if (c->mlp && M >= 0.0) {
+        // the learned indicator decides (TVB test in its uncertainty band)
+        a.mlp = c->mlp;
+        a.mlp_zlo = c->mlp_zlo;
+        a.mlp_zhi = c->mlp_zhi;
+        CK(crk::limit2d_euler_f32_mlp(c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count, c->stream));
+        return CRKDG_OK;
+    }
     CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count,
                            c->stream));
     return CRKDG_OK;
@@ -265,7 +273,7 @@ int enqueue_step(crkdg_ctx* c, double dt, int dt_from_dev, int limit, double M) 
         int r = ensure_partials(c, (size_t)ns * nseg * 8);
         if (r) return r;
         a.partials = c->d_partials;
-        if (c->mlp && limit && M >= 0.0) {
+        if (c->mlp && limit && M >= 0.0 && c->limit_mode == CRKDG_LIMIT_FUSED) {
             a.mlp = c->mlp;
             a.mlp_zlo = c->mlp_zlo;
             a.mlp_zhi = c->mlp_zhi;

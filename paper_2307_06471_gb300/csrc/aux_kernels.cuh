@@ -4,6 +4,7 @@
 #pragma once
 #include "common.cuh"
 #include "limiter.cuh"
+#include "mlp_warp.cuh"
 
 // resident blocks per SM the limiter pass is compiled for (tuning knob)
 #ifndef CRK_LIMIT_MINB
@@ -146,22 +147,22 @@ __global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict_
 // neighbours' averages (mode 0) and writes only its own modes 1.. , so no
 // thread writes anything another thread reads.  The x neighbours' averages
 // come from the neighbouring lanes by shuffle (loads only at a warp's ends
-// and at the domain's sides).  Counts troubled cells (one atomic per warp
-// that has any).  6 blocks per SM (80 registers): at 8 the kernel spills,
-// and it measured 0.0359 ms per pass on the 1920x480 P^2 state against
-// 0.0370 (8 blocks) and 0.0389 (5 blocks).
+// and at the domain's sides).  Returns whether the cell was troubled.
 // The state's time (for time-dependent ghost averages) comes from the device
-// run state when the run is device driven.  Launched with 128 threads per
-// block along x, one block row per mesh row.
-template <class T, int K, int B, int PHYS>
-__global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
-                                                                      unsigned long long* flag_count) {
+// run state when the run is device driven.  (x, y): the thread's cell; lanes
+// past the east side (x >= nx) take part in the shuffles (and, with MLPI, in
+// the warp's network evaluation) and limit nothing.
+// MLPI: the troubled-cell decision comes from the learned indicator (limit
+// if the logit exceeds zhi, keep if it is below zlo, TVB test in between),
+// evaluated for the warp's 32 cells with the weights mw and the warp's
+// staging area.
+template <class T, int K, int B, int PHYS, bool MLPI>
+__device__ __forceinline__ bool limit2d_cell(const StepArgs& a, T* __restrict__ u, int x, int y,
+                                             const MlpSmem* mw, __nv_bfloat16* stage) {
     constexpr int NM = Tab2D<K, B>::NM;
     constexpr int NV = Phys<T, PHYS>::NV;
     const int nx = a.nx, ny = a.ny;
     const size_t plane = (size_t)nx * ny;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const bool inside = x < nx;
     const int xc = inside ? x : nx - 1;   // lanes past the east side mirror the last cell (shuffles only)
@@ -208,19 +209,30 @@ __global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const Step
             tg = a.dt_from_dev ? a.ds->t : a.t;
         }, out);
     };
-    bool fl = false;
     if (inside) {
         if (!perx && x == 0) ghost(0, -1, y, nbW);
         if (!perx && x == nx - 1) ghost(1, nx, y, nbE);
         if (!pery && y == 0) ghost(2, x, -1, nbS);
         if (!pery && y == ny - 1) ghost(3, x, ny, nbN);
+    }
+    int mode = -1;
+    if constexpr (MLPI) {
+        // every lane of the warp takes part (lanes past the side on a copy
+        // of the last cell); features of the cell and its four neighbours
+        float feat[MLP_IN];
+        mlp_features<T, NM>(c, nbE, nbW, nbN, nbS, a.mlp_scale, feat);
+        const float z = mlp_warp_logit(*mw, feat, stage);
+        mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
+    }
+    bool fl = false;
+    if (inside) {
         T Mdx2, Mdy2, gam, ppe;
         if constexpr (sizeof(T) == 4) {
             Mdx2 = a.Mdx2f; Mdy2 = a.Mdy2f; gam = a.gammaf; ppe = a.pp_epsf;
         } else {
             Mdx2 = a.M * a.dx * a.dx; Mdy2 = a.M * a.dy * a.dy; gam = a.gamma; ppe = a.pp_eps;
         }
-        if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam);
+        if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam, mode);
         bool sc = false;
         if (a.pp_on) sc = positivity_cell<T, NV, NM, K, B>(c, gam, ppe);
         if (fl || sc)
@@ -229,8 +241,48 @@ __global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const Step
 #pragma unroll
                 for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x] = c[v][m];
     }
+    return fl;
+}
+
+// The limiter pass: 128 threads per block along x, one block row per mesh
+// row.  Counts troubled cells (one atomic per warp that has any).  6 blocks
+// per SM (80 registers): at 8 the kernel spills, and it measured 0.0359 ms
+// per pass on the 1920x480 P^2 state against 0.0370 (8 blocks) and 0.0389 (5
+// blocks).
+template <class T, int K, int B, int PHYS>
+__global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
+                                                                      unsigned long long* flag_count) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool fl = limit2d_cell<T, K, B, PHYS, false>(a, u, x, blockIdx.y, nullptr, nullptr);
     const unsigned b = __ballot_sync(0xffffffffu, fl);
-    if (lane == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
+}
+
+// The limiter pass with the learned indicator (2D Euler): a grid of a few
+// blocks per SM loads the network's BF16 weights into shared memory once per
+// block and then walks the mesh in tiles of one row x blockDim.x cells
+// (grid-stride), each warp evaluating the network for its 32 cells on the
+// tensor cores.  Shared memory: the weights, then one staging area per warp.
+constexpr int LIMIT_MLP_THREADS = 256;
+template <class T, int K, int B>
+__global__ void __launch_bounds__(LIMIT_MLP_THREADS) limit2d_mlp_kernel(const StepArgs a, T* __restrict__ u,
+                                                                        unsigned long long* flag_count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem& mw = *reinterpret_cast<MlpSmem*>(smem_raw);
+    __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem_raw + sizeof(MlpSmem)) +
+                           (threadIdx.x >> 5) * (32 * MLP_INP + 64);
+    mlp_load_smem(mw, a.mlp);
+    __syncthreads();
+    const int xt = (a.nx + LIMIT_MLP_THREADS - 1) / LIMIT_MLP_THREADS;
+    const long long tiles = (long long)xt * a.ny;
+    unsigned cnt = 0;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int y = (int)(tile / xt);
+        const int x = (int)(tile % xt) * LIMIT_MLP_THREADS + threadIdx.x;
+        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, true>(a, u, x, y, &mw, stage);
+        cnt += __popc(__ballot_sync(0xffffffffu, fl));
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(flag_count, (unsigned long long)cnt);
 }
 
 // out = alpha * x + beta * y over n elements (RKDG Shu--Osher combinations)

@@ -82,6 +82,7 @@ struct StepArgs {
     float lin_kf[6];
     const float* mlp;         // learned indicator parameters (device), or null
     float mlp_zlo, mlp_zhi;   // logit band in which the TVB test decides
+    float mlp_scale;          // M h^2, h = max(dx, dy): the features' scale reference (set_derived)
 };
 
 // -------------------------------------------------------------------------
@@ -385,6 +386,8 @@ inline void set_derived(StepArgs& a) {
     a.lin_k[4] = -a.beta[1] / a.dy;
     a.lin_k[5] = a.beta[1] / a.dy;
     for (int i = 0; i < 6; ++i) a.lin_kf[i] = (float)a.lin_k[i];
+    const double hh = a.dx > a.dy ? a.dx : a.dy;
+    a.mlp_scale = (float)(a.M * hh * hh);
 }
 
 // Device tableau buffer: FP64 a (MAXS x MAXS, row-major), b, c, followed by

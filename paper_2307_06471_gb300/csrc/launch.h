@@ -65,8 +65,11 @@ cudaError_t reduce_euler_f32c(const void* u, int nx, int ny, int nm, double dx, 
 cudaError_t step2d_euler_f32d(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
 cudaError_t info2d_euler_f32d(int k, int basis, int s, KernelInfo* info);
 
-// FP32 2D Euler k = 2 step with the fused learned indicator
+// FP32 2D Euler k = 2 step with the fused learned indicator, and the
+// limiter pass that evaluates the indicator
 cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t limit2d_euler_f32_mlp(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
+                                  cudaStream_t st);
 
 // out = alpha x + beta y (n elements of the state precision), and DevState.t = t
 cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,

@@ -30,107 +30,67 @@ __device__ __forceinline__ T tvb_minmod(T a1, T a2, T a3, T Mh2) {
     return fabs(a1) <= Mh2 ? a1 : minmod3(a1, a2, a3);
 }
 
-// Left (L) and right (R) eigenvectors of the 2D Euler flux Jacobian along
-// AXIS at state u; R columns for eigenvalues (vn - c, vn, vn, vn + c).
-template <class T, int AXIS>
-__device__ __forceinline__ void euler_eig(const T* u, T gamma, T R[4][4], T L[4][4]) {
+// The scalars both directions' eigenvectors share at one state: velocity,
+// |vel|^2, sound speed and its inverse, (gamma-1)/c^2 and its kinetic
+// multiple, total enthalpy -- one reciprocal of rho, one square root, one
+// reciprocal of c per cell for x and y together.
+template <class T>
+struct EulerEig {
+    T w, v, q2, c, ic, b1, b2, H;
+};
+
+template <class T>
+__device__ __forceinline__ EulerEig<T> euler_eig_scalars(const T* u, T gamma) {
+    EulerEig<T> e;
     const T gm1 = gamma - T(1);
     const T ir = T(1) / u[0];
-    const T w = u[1] * ir, v = u[2] * ir;
-    const T q2 = w * w + v * v;
-    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
+    e.w = u[1] * ir;
+    e.v = u[2] * ir;
+    e.q2 = e.w * e.w + e.v * e.v;
+    const T p = gm1 * (u[3] - T(0.5) * u[0] * e.q2);
     const T c2 = gamma * p * ir;
-    const T c = sqrt(c2 > T(0) ? c2 : T(0));
-    const T H = (u[3] + p) * ir;
-    const T vn = AXIS == 0 ? w : v;   // normal velocity
-    const T vt = AXIS == 0 ? v : w;   // tangential velocity
-    const int in = 1 + AXIS;          // normal momentum index
-    const int it = 2 - AXIS;          // tangential momentum index
-    // right eigenvectors (columns)
-    R[0][0] = T(1); R[0][1] = T(1); R[0][2] = T(0); R[0][3] = T(1);
-    R[in][0] = vn - c; R[in][1] = vn; R[in][2] = T(0); R[in][3] = vn + c;
-    R[it][0] = vt; R[it][1] = vt; R[it][2] = T(1); R[it][3] = vt;
-    R[3][0] = H - vn * c; R[3][1] = T(0.5) * q2; R[3][2] = vt; R[3][3] = H + vn * c;
-    // left eigenvectors (rows of R^{-1})
-    const T ic = T(1) / c;
-    const T b1 = gm1 * ic * ic;
-    const T b2 = T(0.5) * b1 * q2;
-    const T wv[2] = {w, v};
-    // acoustic (vn - c)
-    L[0][0] = T(0.5) * (b2 + vn * ic);
-    L[0][in] = -T(0.5) * (b1 * vn + ic);
-    L[0][it] = -T(0.5) * b1 * vt;
-    L[0][3] = T(0.5) * b1;
-    // entropy
-    L[1][0] = T(1) - b2;
-    L[1][in] = b1 * vn;
-    L[1][it] = b1 * vt;
-    L[1][3] = -b1;
-    // shear
+    e.c = sqrt(c2 > T(0) ? c2 : T(0));
+    e.ic = T(1) / e.c;
+    e.b1 = gm1 * e.ic * e.ic;
+    e.b2 = T(0.5) * e.b1 * e.q2;
+    e.H = (u[3] + p) * ir;
+    return e;
+}
+
+// rows of R^{-1} along AXIS (left eigenvectors) from the shared scalars
+template <class T, int AXIS>
+__device__ __forceinline__ void euler_left_of(const EulerEig<T>& e, T L[4][4]) {
+    const T vn = AXIS == 0 ? e.w : e.v;
+    const T vt = AXIS == 0 ? e.v : e.w;
+    const int in = 1 + AXIS, it = 2 - AXIS;
+    L[0][0] = T(0.5) * (e.b2 + vn * e.ic);
+    L[0][in] = -T(0.5) * (e.b1 * vn + e.ic);
+    L[0][it] = -T(0.5) * e.b1 * vt;
+    L[0][3] = T(0.5) * e.b1;
+    L[1][0] = T(1) - e.b2;
+    L[1][in] = e.b1 * vn;
+    L[1][it] = e.b1 * vt;
+    L[1][3] = -e.b1;
     L[2][0] = -vt;
     L[2][in] = T(0);
     L[2][it] = T(1);
     L[2][3] = T(0);
-    // acoustic (vn + c)
-    L[3][0] = T(0.5) * (b2 - vn * ic);
-    L[3][in] = -T(0.5) * (b1 * vn - ic);
-    L[3][it] = -T(0.5) * b1 * vt;
-    L[3][3] = T(0.5) * b1;
-    (void)wv;
+    L[3][0] = T(0.5) * (e.b2 - vn * e.ic);
+    L[3][in] = -T(0.5) * (e.b1 * vn - e.ic);
+    L[3][it] = -T(0.5) * e.b1 * vt;
+    L[3][3] = T(0.5) * e.b1;
 }
 
-// Left eigenvectors only (the troubled-cell test needs L; R only when a cell
-// is limited).
+// columns = right eigenvectors along AXIS, for the eigenvalues (vn - c, vn, vn, vn + c)
 template <class T, int AXIS>
-__device__ __forceinline__ void euler_left(const T* u, T gamma, T L[4][4]) {
-    const T gm1 = gamma - T(1);
-    const T ir = T(1) / u[0];
-    const T w = u[1] * ir, v = u[2] * ir;
-    const T q2 = w * w + v * v;
-    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
-    const T c2 = gamma * p * ir;
-    const T c = sqrt(c2 > T(0) ? c2 : T(0));
-    const T vn = AXIS == 0 ? w : v;
-    const T vt = AXIS == 0 ? v : w;
-    const int in = 1 + AXIS, it = 2 - AXIS;
-    const T ic = T(1) / c;
-    const T b1 = gm1 * ic * ic;
-    const T b2 = T(0.5) * b1 * q2;
-    L[0][0] = T(0.5) * (b2 + vn * ic);
-    L[0][in] = -T(0.5) * (b1 * vn + ic);
-    L[0][it] = -T(0.5) * b1 * vt;
-    L[0][3] = T(0.5) * b1;
-    L[1][0] = T(1) - b2;
-    L[1][in] = b1 * vn;
-    L[1][it] = b1 * vt;
-    L[1][3] = -b1;
-    L[2][0] = -vt;
-    L[2][in] = T(0);
-    L[2][it] = T(1);
-    L[2][3] = T(0);
-    L[3][0] = T(0.5) * (b2 - vn * ic);
-    L[3][in] = -T(0.5) * (b1 * vn - ic);
-    L[3][it] = -T(0.5) * b1 * vt;
-    L[3][3] = T(0.5) * b1;
-}
-
-template <class T, int AXIS>
-__device__ __forceinline__ void euler_right(const T* u, T gamma, T R[4][4]) {
-    const T gm1 = gamma - T(1);
-    const T ir = T(1) / u[0];
-    const T w = u[1] * ir, v = u[2] * ir;
-    const T q2 = w * w + v * v;
-    const T p = gm1 * (u[3] - T(0.5) * u[0] * q2);
-    const T c2 = gamma * p * ir;
-    const T c = sqrt(c2 > T(0) ? c2 : T(0));
-    const T H = (u[3] + p) * ir;
-    const T vn = AXIS == 0 ? w : v;
-    const T vt = AXIS == 0 ? v : w;
+__device__ __forceinline__ void euler_right_of(const EulerEig<T>& e, T R[4][4]) {
+    const T vn = AXIS == 0 ? e.w : e.v;
+    const T vt = AXIS == 0 ? e.v : e.w;
     const int in = 1 + AXIS, it = 2 - AXIS;
     R[0][0] = T(1); R[0][1] = T(1); R[0][2] = T(0); R[0][3] = T(1);
-    R[in][0] = vn - c; R[in][1] = vn; R[in][2] = T(0); R[in][3] = vn + c;
+    R[in][0] = vn - e.c; R[in][1] = vn; R[in][2] = T(0); R[in][3] = vn + e.c;
     R[it][0] = vt; R[it][1] = vt; R[it][2] = T(1); R[it][3] = vt;
-    R[3][0] = H - vn * c; R[3][1] = T(0.5) * q2; R[3][2] = vt; R[3][3] = H + vn * c;
+    R[3][0] = e.H - vn * e.c; R[3][1] = T(0.5) * e.q2; R[3][2] = vt; R[3][3] = e.H + vn * e.c;
 }
 
 // Limit one cell in place.  u[v][m] modal coefficients, nb* neighbour
@@ -149,8 +109,9 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
     bool flag = false;
     if (NV == 4) {
         T L[4][4], mxc[4], myc[4];
+        const EulerEig<T> eg = euler_eig_scalars<T>(avg, gamma);
         // x direction: characteristic values and the modified minmod
-        euler_left<T, 0>(avg, gamma, L);
+        euler_left_of<T, 0>(eg, L);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             T s1 = 0, s2 = 0, s3 = 0;
@@ -164,7 +125,7 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
             flag |= (mxc[f] != s1);
         }
         // y direction
-        euler_left<T, 1>(avg, gamma, L);
+        euler_left_of<T, 1>(eg, L);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             T s1 = 0, s2 = 0, s3 = 0;
@@ -181,7 +142,7 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
         if (flag) {
             // back to conserved variables only for limited cells
             T R[4][4];
-            euler_right<T, 0>(avg, gamma, R);
+            euler_right_of<T, 0>(eg, R);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 T s = 0;
@@ -189,7 +150,7 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
                 for (int f = 0; f < 4; ++f) s += R[v][f] * mxc[f];
                 mx[v] = s;
             }
-            euler_right<T, 1>(avg, gamma, R);
+            euler_right_of<T, 1>(eg, R);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 T s = 0;

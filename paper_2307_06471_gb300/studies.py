@@ -345,10 +345,15 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
     net = nets[0]
     # 4. throughput at 2048 x 2048 (device steps, L2 not a factor at 403 MB)
     nx, ny = perf_n
-    for name, prec, use_net in (("f32_tvb", B.F32, False), ("f32_mlp", B.F32, True), ("f64_tvb", B.F64, False)):
+    # (the network in the limiter pass, the default limit mode, and fused
+    # into the step's load)
+    for name, prec, use_net, fused in (("f32_tvb", B.F32, False, False), ("f32_mlp", B.F32, True, False),
+                                       ("f32_mlp_fused", B.F32, True, True), ("f64_tvb", B.F64, False, False)):
         s = _shock_vortex_solver(B, GTB, inp, nx, ny, prec, sh)
         if use_net:
             s.set_indicator(net)
+        if fused:
+            s.set_limit_mode(B.LIMIT_FUSED)
         n_steps = perf_steps if prec == B.F32 else max(5, perf_steps // 10)
         s.advance(3, 0.16, 10.0)
         torch.cuda.synchronize()

@@ -130,14 +130,17 @@ def test_training_learns_a_separable_rule():
     net.close()
 
 
+@pytest.mark.parametrize("where", ["fused", "pass"])
 @pytest.mark.parametrize("mode", ["always", "never", "tvb_band"])
-def test_fused_indicator_decisions(mode):
+def test_fused_indicator_decisions(mode, where):
     """A network whose output is a constant logit forces the decision (all
-    cells limited / none); a band covering every logit leaves it to TVB."""
+    cells limited / none); a band covering every logit leaves it to TVB.  The
+    indicator runs fused into the step's load or in the limiter pass."""
     import torch
     from paper_2307_06471_gb300 import binding as B
     nx, ny, M = 64, 40, 20.0
     gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), 2, "P", "euler", "ssprk3", OUT, "f32")
+    gs.set_limit_mode(B.LIMIT_FUSED if where == "fused" else B.LIMIT_PASS)
     u = _state(nx, ny, seed=42)
     u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
     vec = np.zeros(11009, dtype=np.float32)
