@@ -12,7 +12,7 @@ namespace {
 template <int K, int B>
 cudaError_t run_step_c(const StepArgs& a, int wpb, cudaStream_t st) {
     using C = Step2D<float, K, B, PHYS_EULER>;
-    auto kern = step2d_kernel<float, K, B, PHYS_EULER, true>;
+    auto kern = step2d_kernel<float, K, B, PHYS_EULER, true, false, false>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -34,7 +34,7 @@ template <int K, int B>
 cudaError_t run_info_c(int s, KernelInfo* info) {
     using C = Step2D<float, K, B, PHYS_EULER>;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, step2d_kernel<float, K, B, PHYS_EULER, true>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, step2d_kernel<float, K, B, PHYS_EULER, true, false, false>);
     if (e != cudaSuccess) return e;
     info->regs = fa.numRegs;
     info->max_threads = fa.maxThreadsPerBlock;

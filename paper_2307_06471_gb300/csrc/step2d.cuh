@@ -68,6 +68,42 @@ __device__ __forceinline__ void pfma(T& a0, T& a1, T x0, T x1, T c) {
     }
 }
 
+// packed sum, difference and scaling of pairs: one FP32x2 instruction each
+// on sm_100+ for float (rounding as the scalar operations), scalar for double
+template <class T>
+__device__ __forceinline__ void padd(T& r0, T& r1, T a0, T a1, T b0, T b1) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = __fadd2_rn(make_float2(a0, a1), make_float2(b0, b1));
+        r0 = r.x;
+        r1 = r.y;
+    } else {
+        r0 = a0 + b0;
+        r1 = a1 + b1;
+    }
+}
+template <class T>
+__device__ __forceinline__ void psub(T& r0, T& r1, T a0, T a1, T b0, T b1) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = __ffma2_rn(make_float2(b0, b1), make_float2(-1.f, -1.f), make_float2(a0, a1));
+        r0 = r.x;
+        r1 = r.y;
+    } else {
+        r0 = a0 - b0;
+        r1 = a1 - b1;
+    }
+}
+template <class T>
+__device__ __forceinline__ void pmul(T& a0, T& a1, T c) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = __fmul2_rn(make_float2(a0, a1), make_float2(c, c));
+        a0 = r.x;
+        a1 = r.y;
+    } else {
+        a0 *= c;
+        a1 *= c;
+    }
+}
+
 template <class T, int K, int B, int PHYS>
 struct Step2D {
     using TB = Tab2D<K, B>;
@@ -574,9 +610,10 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             for (int m = 0; m < NM; ++m) un[v][m] = uin[(size_t)(v * NM + m) * plane + cidx];
 
         // DEV: the base cb = hi part of the average; un becomes the deviation
-        // (lo of the average, hi + lo of the higher modes); dcE / dcW / dcS are
-        // the east / west / south neighbours' bases minus this cell's
-        T cb[NV], dcE[NV], dcW[NV], dcS[NV];
+        // (lo of the average, hi + lo of the higher modes); cS is the base of
+        // the row below.  The neighbours' bases minus this cell's are formed
+        // where they are used (fewer live registers)
+        T cb[NV], cS[NV];
         if constexpr (DEV) {
             const size_t lo_off = (size_t)C::NDOF * plane;
 #pragma unroll
@@ -589,9 +626,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             ph.set_base(cb);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                dcE[v] = shfl_down(cb[v], 1) - cb[v];
-                dcW[v] = shfl_up(cb[v], 1) - cb[v];
-                dcS[v] = cprev[v] - cb[v];
+                cS[v] = cprev[v];
                 cprev[v] = cb[v];
             }
         }
@@ -762,23 +797,31 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         for (int m = 0; m < NM; ++m) V(v, m) += bi * vol[v][m];
                 }
             }
-            // face traces
+            // face traces.  phi_m(-1, eta) = (-1)^i phi_m(1, eta): the east and
+            // west traces are the sum and difference of the even-i and odd-i
+            // parts of one contraction (north and south likewise in j)
             T tE[NQ][NV], tW[NQ][NV], tN[NQ][NV], tS[NQ][NV];
             if constexpr (NV % 2 == 0) {
 #pragma unroll
                 for (int p = 0; p < NQ; ++p)
 #pragma unroll
                     for (int v = 0; v < NV; v += 2) {
-                        T e0 = 0, e1 = 0, w0 = 0, w1 = 0, n0 = 0, n1 = 0, s0 = 0, s1 = 0;
+                        T xe0 = 0, xe1 = 0, xo0 = 0, xo1 = 0, ye0 = 0, ye1 = 0, yo0 = 0, yo1 = 0;
 #pragma unroll
                         for (int m = 0; m < NM; ++m) {
-                            pfma(e0, e1, w[v][m], w[v + 1][m], T(tb.tE[p][m]));
-                            pfma(w0, w1, w[v][m], w[v + 1][m], T(tb.tW[p][m]));
-                            pfma(n0, n1, w[v][m], w[v + 1][m], T(tb.tN[p][m]));
-                            pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.tS[p][m]));
+                            if (tb.tE[p][m] != 0.0) {
+                                if (tb.ip[m] == 0) pfma(xe0, xe1, w[v][m], w[v + 1][m], T(tb.tE[p][m]));
+                                else pfma(xo0, xo1, w[v][m], w[v + 1][m], T(tb.tE[p][m]));
+                            }
+                            if (tb.tN[p][m] != 0.0) {
+                                if (tb.jp[m] == 0) pfma(ye0, ye1, w[v][m], w[v + 1][m], T(tb.tN[p][m]));
+                                else pfma(yo0, yo1, w[v][m], w[v + 1][m], T(tb.tN[p][m]));
+                            }
                         }
-                        tE[p][v] = e0; tE[p][v + 1] = e1; tW[p][v] = w0; tW[p][v + 1] = w1;
-                        tN[p][v] = n0; tN[p][v + 1] = n1; tS[p][v] = s0; tS[p][v + 1] = s1;
+                        padd(tE[p][v], tE[p][v + 1], xe0, xe1, xo0, xo1);
+                        psub(tW[p][v], tW[p][v + 1], xe0, xe1, xo0, xo1);
+                        padd(tN[p][v], tN[p][v + 1], ye0, ye1, yo0, yo1);
+                        psub(tS[p][v], tS[p][v + 1], ye0, ye1, yo0, yo1);
                     }
             } else {
 #pragma unroll
@@ -848,16 +891,28 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         slot(offNF + (i * NQ + p) * (NV + 1) + NV) = sN;
                     }
                     if constexpr (NV % 2 == 0) {
+                        // pW = (-1)^i pE, pS = (-1)^j pN: fe pE - fw pW = pE (fe -+ fw)
 #pragma unroll
                         for (int v = 0; v < NV; v += 2) {
-                            const T ge0 = rx * fe[v], ge1 = rx * fe[v + 1], gw0 = rx * fw[v], gw1 = rx * fw[v + 1];
-                            const T gn0 = ry * fn[v], gn1 = ry * fn[v + 1], gs0 = ry * fs[v], gs1 = ry * fs[v + 1];
+                            T xm0, xm1, xp0, xp1, ym0, ym1, yp0, yp1;
+                            psub(xm0, xm1, fe[v], fe[v + 1], fw[v], fw[v + 1]);
+                            padd(xp0, xp1, fe[v], fe[v + 1], fw[v], fw[v + 1]);
+                            psub(ym0, ym1, fn[v], fn[v + 1], fs[v], fs[v + 1]);
+                            padd(yp0, yp1, fn[v], fn[v + 1], fs[v], fs[v + 1]);
+                            pmul(xm0, xm1, rx);
+                            pmul(xp0, xp1, rx);
+                            pmul(ym0, ym1, ry);
+                            pmul(yp0, yp1, ry);
 #pragma unroll
                             for (int m = 0; m < NM; ++m) {
-                                if (tb.pE[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], ge0, ge1, T(tb.pE[p][m]));
-                                if (tb.pW[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gw0, gw1, -T(tb.pW[p][m]));
-                                if (tb.pN[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gn0, gn1, T(tb.pN[p][m]));
-                                if (tb.pS[p][m] != 0.0) pfma(floc[v][m], floc[v + 1][m], gs0, gs1, -T(tb.pS[p][m]));
+                                if (tb.pE[p][m] != 0.0) {
+                                    if (tb.ip[m] == 0) pfma(floc[v][m], floc[v + 1][m], xm0, xm1, T(tb.pE[p][m]));
+                                    else pfma(floc[v][m], floc[v + 1][m], xp0, xp1, T(tb.pE[p][m]));
+                                }
+                                if (tb.pN[p][m] != 0.0) {
+                                    if (tb.jp[m] == 0) pfma(floc[v][m], floc[v + 1][m], ym0, ym1, T(tb.pN[p][m]));
+                                    else pfma(floc[v][m], floc[v + 1][m], yp0, yp1, T(tb.pN[p][m]));
+                                }
                             }
                         }
                     } else {
@@ -878,6 +933,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             if (!need_flux) continue;
             // east face: own east trace vs. the west trace of the lane to the right
             if (out_row && !fuseE) {
+                T dcE[NV];   // DEV: east neighbour's base minus this cell's
+                if constexpr (DEV) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) dcE[v] = shfl_down(cb[v], 1) - cb[v];
+                }
 #pragma unroll
                 for (int p = 0; p < NQ; ++p)
 #pragma unroll
@@ -972,7 +1032,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                         for (int v = 0; v < NV; ++v) {
                             lo[p][v] = slot(offN + (i * NQ + p) * NV + v);
-                            if constexpr (DEV) lo[p][v] += dcS[v];
+                            if constexpr (DEV) lo[p][v] += cS[v] - cb[v];
                         }
                 }
 #pragma unroll
@@ -1095,7 +1155,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             // DEV: FS is relative to this row's base; the row below takes it
             // relative to its own: minus f_y(c_below) - f_y(c) (sum_i b_i = 1)
             T gS[NV];
-            if constexpr (DEV) ph.template fluxn<1>(dcS, gS);
+            if constexpr (DEV) {
+                T dcS[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dcS[v] = cS[v] - cb[v];
+                ph.template fluxn<1>(dcS, gS);
+            }
             T P[NV][NM];
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -1122,7 +1187,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
             for (int v = 0; v < NV; ++v) FW[p][v] = shfl_up(FE[p][v], 1);
         if constexpr (DEV) {
-            T gW[NV];
+            T gW[NV], dcW[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dcW[v] = shfl_up(cb[v], 1) - cb[v];
             ph.template fluxn<0>(dcW, gW);
 #pragma unroll
             for (int p = 0; p < NQ; ++p)

@@ -97,6 +97,7 @@ struct Tab2D {
     double tE[NQ][NM], tW[NQ][NM], tN[NQ][NM], tS[NQ][NM];   // phi_m at face points
     double pE[NQ][NM], pW[NQ][NM], pN[NQ][NM], pS[NQ][NM];   // w_p phi_m at face points
     double sN[NM];         // sum_p pN[p][m] = int phi_m(xi, 1) dxi = 2 if i = 0, else 0 (exact rule)
+    int ip[NM], jp[NM];    // parities of i and j: phi_m(-1, eta) = (-1)^i phi_m(1, eta), likewise in eta
     double cm[NM];         // (2i+1)(2j+1)/2 = inverse mass / (2|K|) factor
     double pw[NQV][NM];    // projection weights 1/4 w_q phi_m(q) / mass_m
     double xq[NQ];         // Gauss nodes
@@ -114,6 +115,8 @@ constexpr Tab2D<K, B> make_tab2d() {
         const double mass = 1.0 / ((2.0 * i + 1.0) * (2.0 * j + 1.0));
         t.cm[m] = 0.5 / mass;
         t.sN[m] = i == 0 ? 2.0 : 0.0;
+        t.ip[m] = i & 1;
+        t.jp[m] = j & 1;
         for (int a = 0; a < NQ; ++a)
             for (int b = 0; b < NQ; ++b) {
                 const int q = a * NQ + b;

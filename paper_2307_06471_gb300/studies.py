@@ -611,10 +611,15 @@ def dmr_full(nx=1920, ny=480, k=2, T=0.2, cfl=None, precision="f32"):
             "p_min": float(p.min()), "p_max": float(p.max()), "troubled_last_step": int(troubled)}
 
 
+def build_lib():
+    from paper_2307_06471_gb300 import build
+    build.build()
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d",
-                                     "advection_hbm", "dmr_full"])
+                                     "advection_hbm", "dmr_full", "precision_rates", "matched_l1"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -633,6 +638,14 @@ if __name__ == "__main__":
         r = advection2d_inflow()
     elif a.study == "advection_hbm":   # --sizes N,steps (a smaller case, e.g. for a profiler)
         r = advection_hbm(*(int(v) for v in a.sizes.split(",")[:2])) if a.sizes != "80,160,320" else advection_hbm()
+    elif a.study == "precision_rates":   # --sizes N --steps K --precision f32,f32d,...
+        build_lib()
+        r = precision_rates(int(a.sizes.split(",")[0]) if a.sizes != "80,160,320" else 1280, a.steps,
+                            variants=tuple(a.precision.split(",")) if a.precision != "f32" else
+                            ("f32", "f32c", "f32d", "f64"))
+    elif a.study == "matched_l1":
+        build_lib()
+        r = matched_l1(T=a.T if a.T != 10.0 else 1.0)
     elif a.study == "dmr_full":
         r = dmr_full(*(int(v) for v in a.sizes.split(",")[:3])) if a.sizes != "80,160,320" else dmr_full()
     else:
