@@ -1,11 +1,15 @@
 """Algorithmic work of one fused cRKDG step per cell (for roofline figures).
 
-Counts the floating-point operations that the 2D step kernel performs for
-one interior cell (halo recomputation excluded), from the structure of the
-kernel's loops: an FMA counts 2, add/sub/mul/div/sqrt/max count 1.  Products
-with a zero basis-table entry that the kernel skips at compile time (the
-derivative tables) are not counted; products with zero point values (which
-the kernel does not skip) are counted.
+Counts the floating-point operations of the quadrature form of one cRKDG
+step for one interior cell (halo recomputation excluded): every point
+value, face trace and projection as a direct sum over the modes, as eq.
+(2.3) and (2.7) define them; an FMA counts 2, add/sub/mul/div/sqrt/max
+count 1.  Products with a zero derivative-table entry are not counted;
+products with zero point values are.  The count is the method's and does
+not follow implementation shortcuts: the 2D step kernel forms the east/west
+(north/south) traces and face projections from even- and odd-mode partial
+sums (phi_m(-1, eta) = (-1)^i phi_m(1, eta)), about 13 % fewer operations
+for P^2 than counted here.
 
 Bytes: u^n is read once and u^{n+1} written once per cell: 2 * NDOF * size,
 plus, with the limiter, the neighbours' averages (served by L1/L2 in the
