@@ -338,6 +338,14 @@ int crkdg_batch_positivity(crkdg_batch* b, double eps);
  * graph (reads one counter). */
 int crkdg_batch_run(crkdg_batch* b, double cfl, double t_end, int steps_per_graph, int max_graphs, int* n_done);
 int crkdg_batch_problem_info(crkdg_batch* b, int problem, double* t, unsigned long long* steps, unsigned* status);
+/* where the pending limiter of every problem runs (as crkdg_set_limit_mode):
+ * CRKDG_LIMIT_PASS (default) one in-place pass over every running problem's
+ * cells (tiles of 128 cells of a row) before the batched step, which then
+ * loads the limited states; CRKDG_LIMIT_FUSED inside the batched step's
+ * load.  Problems that reached t_end are not limited by the pass (their
+ * stored state keeps its pending limit, which get_state applies).  EINVAL
+ * for another mode. */
+int crkdg_batch_set_limit_mode(crkdg_batch* b, int mode);
 /* launch shape (rows per warp segment, warps per block) and its autotuner,
  * which times one batched step per candidate on the current states (run
  * states restored afterwards) */

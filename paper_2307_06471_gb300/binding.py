@@ -102,6 +102,7 @@ _SIGS = {
     "crkdg_batch_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_batch_positivity": (C.c_int, [C.c_void_p, C.c_double]),
     "crkdg_batch_run": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "crkdg_batch_set_limit_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "crkdg_batch_problem_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_ulonglong),
                                            C.POINTER(C.c_uint)]),
     "crkdg_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -451,6 +452,9 @@ class Batch:
         a = np.empty((4, self.n_modes, ny, nx))
         _bcheck(lib().crkdg_batch_get_state(self.ptr, p, _dptr(a)))
         return a
+
+    def set_limit_mode(self, mode):
+        _bcheck(lib().crkdg_batch_set_limit_mode(self.ptr, int(mode)))
 
     def limit(self, M):
         _bcheck(lib().crkdg_batch_limit(self.ptr, float(M)))

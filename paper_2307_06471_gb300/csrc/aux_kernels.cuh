@@ -156,12 +156,23 @@ __global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict_
 // if the logit exceeds zhi, keep if it is below zlo, TVB test in between),
 // evaluated for the warp's 32 cells with the weights mw and the warp's
 // staging area.
+// The mesh a limiter pass works on: a single problem's (from the launch
+// arguments) or one problem of a batch (from its table entry), the time of
+// its ghost data (tsrc: the device run state, or null for a.t) and its TVB
+// thresholds M dx^2, M dy^2 in the kernel's arithmetic.
+struct LimMesh {
+    int nx, ny;
+    double x0, y0, dx, dy;
+    const DevState* tsrc;
+    double Mdx2, Mdy2;
+};
+
 template <class T, int K, int B, int PHYS, bool MLPI>
-__device__ __forceinline__ bool limit2d_cell(const StepArgs& a, T* __restrict__ u, int x, int y,
+__device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g, T* __restrict__ u, int x, int y,
                                              const MlpSmem* mw, __nv_bfloat16* stage) {
     constexpr int NM = Tab2D<K, B>::NM;
     constexpr int NV = Phys<T, PHYS>::NV;
-    const int nx = a.nx, ny = a.ny;
+    const int nx = g.nx, ny = g.ny;
     const size_t plane = (size_t)nx * ny;
     const int lane = threadIdx.x & 31;
     const bool inside = x < nx;
@@ -204,9 +215,9 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, T* __restrict__ 
         cold_branch();
         const int cxc = opaque(cx), cyc = opaque(cy);
         bc_exterior<T, NV>(a.bc[side], side < 2 ? 0 : 1, own, [&](double& xg, double& yg, double& tg) {
-            xg = a.x0 + (cxc + 0.5) * a.dx;
-            yg = a.y0 + (cyc + 0.5) * a.dy;
-            tg = a.dt_from_dev ? a.ds->t : a.t;
+            xg = g.x0 + (cxc + 0.5) * g.dx;
+            yg = g.y0 + (cyc + 0.5) * g.dy;
+            tg = g.tsrc ? g.tsrc->t : a.t;
         }, out);
     };
     if (inside) {
@@ -226,11 +237,12 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, T* __restrict__ 
     }
     bool fl = false;
     if (inside) {
-        T Mdx2, Mdy2, gam, ppe;
+        const T Mdx2 = T(g.Mdx2), Mdy2 = T(g.Mdy2);
+        T gam, ppe;
         if constexpr (sizeof(T) == 4) {
-            Mdx2 = a.Mdx2f; Mdy2 = a.Mdy2f; gam = a.gammaf; ppe = a.pp_epsf;
+            gam = a.gammaf; ppe = a.pp_epsf;
         } else {
-            Mdx2 = a.M * a.dx * a.dx; Mdy2 = a.M * a.dy * a.dy; gam = a.gamma; ppe = a.pp_eps;
+            gam = a.gamma; ppe = a.pp_eps;
         }
         if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam, mode);
         bool sc = false;
@@ -244,6 +256,23 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, T* __restrict__ 
     return fl;
 }
 
+// the mesh view of a single-problem launch: thresholds as set_limiter_params
+// made them (FP32 state) or in FP64
+template <class T>
+__device__ __forceinline__ LimMesh single_mesh(const StepArgs& a) {
+    LimMesh g;
+    g.nx = a.nx;
+    g.ny = a.ny;
+    g.x0 = a.x0;
+    g.y0 = a.y0;
+    g.dx = a.dx;
+    g.dy = a.dy;
+    g.tsrc = a.dt_from_dev ? a.ds : nullptr;
+    g.Mdx2 = sizeof(T) == 4 ? double(a.Mdx2f) : a.M * a.dx * a.dx;
+    g.Mdy2 = sizeof(T) == 4 ? double(a.Mdy2f) : a.M * a.dy * a.dy;
+    return g;
+}
+
 // The limiter pass: 128 threads per block along x, one block row per mesh
 // row.  Counts troubled cells (one atomic per warp that has any).  6 blocks
 // per SM (80 registers): at 8 the kernel spills, and it measured 0.0359 ms
@@ -253,7 +282,7 @@ template <class T, int K, int B, int PHYS>
 __global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
                                                                       unsigned long long* flag_count) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool fl = limit2d_cell<T, K, B, PHYS, false>(a, u, x, blockIdx.y, nullptr, nullptr);
+    const bool fl = limit2d_cell<T, K, B, PHYS, false>(a, single_mesh<T>(a), u, x, blockIdx.y, nullptr, nullptr);
     const unsigned b = __ballot_sync(0xffffffffu, fl);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
 }
@@ -273,16 +302,47 @@ __global__ void __launch_bounds__(LIMIT_MLP_THREADS) limit2d_mlp_kernel(const St
                            (threadIdx.x >> 5) * (32 * MLP_INP + 64);
     mlp_load_smem(mw, a.mlp);
     __syncthreads();
+    const LimMesh g = single_mesh<T>(a);
     const int xt = (a.nx + LIMIT_MLP_THREADS - 1) / LIMIT_MLP_THREADS;
     const long long tiles = (long long)xt * a.ny;
     unsigned cnt = 0;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int y = (int)(tile / xt);
         const int x = (int)(tile % xt) * LIMIT_MLP_THREADS + threadIdx.x;
-        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, true>(a, u, x, y, &mw, stage);
+        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, true>(a, g, u, x, y, &mw, stage);
         cnt += __popc(__ballot_sync(0xffffffffu, fl));
     }
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(flag_count, (unsigned long long)cnt);
+}
+
+// The limiter pass of a batched ensemble: one block of 128 threads per row
+// tile of one problem (rows[b] = problem, row, first column), each problem's
+// current buffer limited in place; problems that reached t_end (dt 0) are
+// left as they are.  Troubled cells count into the problem's run state.
+template <class T, int K, int B>
+__global__ void __launch_bounds__(128, CRK_LIMIT_MINB)
+    batch_limit2d_kernel(const StepArgs a, const BatchProblem* __restrict__ probs, const int4* __restrict__ rows,
+                         DevState* states, const int* curs, T* bufA, T* bufB) {
+    const int4 rt = rows[blockIdx.x];
+    DevState* ds = states + rt.x;
+    if (!(ds->dt > 0.0)) return;   // the whole block: one problem
+    const BatchProblem pb = probs[rt.x];
+    T* u = (curs[rt.x] ? bufB : bufA) + pb.offset;
+    LimMesh g;
+    g.nx = pb.nx;
+    g.ny = pb.ny;
+    g.x0 = pb.x0;
+    g.y0 = pb.y0;
+    g.dx = pb.dx;
+    g.dy = pb.dy;
+    g.tsrc = ds;
+    // the thresholds in the arithmetic set_limiter_params uses for a single problem
+    const double mx2 = a.M * pb.dx * pb.dx, my2 = a.M * pb.dy * pb.dy;
+    g.Mdx2 = sizeof(T) == 4 ? double(float(mx2)) : mx2;
+    g.Mdy2 = sizeof(T) == 4 ? double(float(my2)) : my2;
+    const bool fl = limit2d_cell<T, K, B, PHYS_EULER, false>(a, g, u, rt.z + threadIdx.x, rt.y, nullptr, nullptr);
+    const unsigned b = __ballot_sync(0xffffffffu, fl);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ds->lim_count, (unsigned long long)__popc(b));
 }
 
 // out = alpha * x + beta * y over n elements (RKDG Shu--Osher combinations)

@@ -101,6 +101,9 @@ struct crkdg_batch {
     unsigned long long* d_flags = nullptr;
     cudaStream_t stream = nullptr;
     int seg_rows = 32, wpb = 4;
+    int4* d_rows = nullptr;                // limiter-pass row tiles: (problem, row, first column)
+    int n_rows = 0;
+    int limit_mode = CRKDG_LIMIT_PASS;     // crkdg_batch_set_limit_mode
     bool limiter_on = false, pending = false;
     double M = -1.0, pp_eps = 0.0, M_pending = -1.0, pp_pending = 0.0;
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
@@ -134,10 +137,20 @@ int build_tasks(crkdg_batch* b) {
         for (int i = 0; i < w; ++i) b->tasks.push_back(make_int2(p, i));
         warp0 += w;
     }
+    // the limiter pass's tiles: 128 cells of one row of one problem
+    std::vector<int4> rows;
+    for (int p = 0; p < b->n; ++p)
+        for (int y = 0; y < b->probs[p].ny; ++y)
+            for (int x = 0; x < b->probs[p].nx; x += 128) rows.push_back(make_int4(p, y, x, 0));
     if (b->d_tasks) cudaFree(b->d_tasks);
     if (b->d_partials) cudaFree(b->d_partials);
+    if (b->d_rows) cudaFree(b->d_rows);
     b->d_tasks = nullptr;
     b->d_partials = nullptr;
+    b->d_rows = nullptr;
+    b->n_rows = (int)rows.size();
+    BCK(cudaMalloc(&b->d_rows, rows.size() * sizeof(int4)));
+    BCK(cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(int4), cudaMemcpyHostToDevice));
     BCK(cudaMalloc(&b->d_tasks, b->tasks.size() * sizeof(int2)));
     BCK(cudaMalloc(&b->d_partials, (size_t)warp0 * 8 * sizeof(double)));
     BCK(cudaMemcpy(b->d_tasks, b->tasks.data(), b->tasks.size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -152,6 +165,17 @@ int enqueue_batch_step(crkdg_batch* b, int limit, double M, double pp) {
     a.limit = limit;
     a.M = M;
     a.pp_eps = limit ? pp : 0.0;
+    if (limit && b->limit_mode == CRKDG_LIMIT_PASS) {
+        // the pending limit of every running problem as one in-place pass;
+        // the batched step then loads the limited states as they are
+        cudaError_t e = b->precision == CRKDG_F32
+                            ? crk::blimit2d_euler_f32(b->k, b->basis, a, b->d_probs, b->d_rows, b->n_rows,
+                                                      b->d_states, b->d_curs, b->buf[0], b->buf[1], b->stream)
+                            : crk::blimit2d_euler_f64(b->k, b->basis, a, b->d_probs, b->d_rows, b->n_rows,
+                                                      b->d_states, b->d_curs, b->buf[0], b->buf[1], b->stream);
+        if (e != cudaSuccess) return bfail(CRKDG_ECUDA, std::string("batched limiter pass: ") + cudaGetErrorString(e));
+        a.limit = 0;
+    }
     cudaError_t e = b->precision == CRKDG_F32
                         ? crk::batch2d_euler_f32(b->k, b->basis, a, b->d_probs, b->d_tasks, (int)b->tasks.size(),
                                                  b->d_states, b->d_curs, b->d_done, b->buf[0], b->buf[1], b->wpb,
@@ -273,7 +297,7 @@ void crkdg_batch_destroy(crkdg_batch* b) {
     for (int i = 0; i < 2; ++i)
         if (b->buf[i]) cudaFree(b->buf[i]);
     for (void* p : {(void*)b->d_probs, (void*)b->d_tasks, (void*)b->d_states, (void*)b->d_curs, (void*)b->d_done,
-                    (void*)b->d_partials, (void*)b->d_tab, (void*)b->d_flags})
+                    (void*)b->d_partials, (void*)b->d_tab, (void*)b->d_flags, (void*)b->d_rows})
         if (p) cudaFree(p);
     delete b;
 }
@@ -501,6 +525,15 @@ int crkdg_batch_sizes(const crkdg_batch* b, int* n_problems, long long* total_ce
     if (total_cells) *total_cells = c;
     if (n_modes) *n_modes = b->nm;
     if (n_tasks) *n_tasks = (int)b->tasks.size();
+    return CRKDG_OK;
+}
+
+int crkdg_batch_set_limit_mode(crkdg_batch* b, int mode) {
+    if (!b) return bfail(CRKDG_EINVAL, "null batch");
+    if (mode != CRKDG_LIMIT_FUSED && mode != CRKDG_LIMIT_PASS) return bfail(CRKDG_EINVAL, "unknown limit mode");
+    b->limit_mode = mode;
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
     return CRKDG_OK;
 }
 

@@ -85,6 +85,16 @@ struct StepArgs {
     float mlp_scale;          // M h^2, h = max(dx, dy): the features' scale reference (set_derived)
 };
 
+// One problem of a batched ensemble (problem table, device)
+struct BatchProblem {
+    long long offset;      // element offset of the problem's planes in each buffer
+    int nx, ny;
+    double x0, y0, dx, dy;
+    double rx, ry;         // 1/dx, 1/dy (host)
+    int n_strips, n_segs;
+    int warp0;             // first task / reduction slot of the problem
+};
+
 // -------------------------------------------------------------------------
 // Physical flux along one axis and the wave speed |f'(u).nu| for nu = e_axis.
 template <class T, int PHYS> struct Phys;

@@ -88,7 +88,10 @@ struct BatchProblem;
     cudaError_t batch2d_##NAME(int k, int basis, const StepArgs& a, const BatchProblem* probs, const int2* tasks, \
                                int n_tasks, DevState* states, int* curs, unsigned* done, const void* bufA,    \
                                void* bufB, int wpb, cudaStream_t st);                                         \
-    cudaError_t binfo2d_##NAME(int k, int basis, int s, KernelInfo* info);
+    cudaError_t binfo2d_##NAME(int k, int basis, int s, KernelInfo* info);                                 \
+    cudaError_t blimit2d_##NAME(int k, int basis, const StepArgs& a, const BatchProblem* probs, const int4* rows, \
+                                int n_rows, DevState* states, const int* curs, void* bufA, void* bufB,        \
+                                cudaStream_t st);
 CRK_DECL_B(euler_f32)
 CRK_DECL_B(euler_f64)
 #undef CRK_DECL_B

@@ -747,7 +747,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     for (int v = 0; v < NV; v += 2) {
                         T s0 = T(0), s1 = T(0);
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
+                        for (int m = 0; m < NM; ++m)   // (P_1 vanishes at the middle Gauss point)
+                            if (tb.phi[q][m] != 0.0) pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
                         uq[v] = s0;
                         uq[v + 1] = s1;
                     }
@@ -756,7 +757,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     for (int v = 0; v < NV; ++v) {
                         T s = T(0);
 #pragma unroll
-                        for (int m = 0; m < NM; ++m) s += w[v][m] * T(tb.phi[q][m]);
+                        for (int m = 0; m < NM; ++m)
+                            if (tb.phi[q][m] != 0.0) s += w[v][m] * T(tb.phi[q][m]);
                         uq[v] = s;
                     }
                 }
@@ -1288,16 +1290,8 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MIN
 // (t, dt from its own FP64 wave-speed reduction, t_end, status) and buffer
 // index.  Warps take (problem, warp) tasks from a flattened table.  A problem
 // whose dt is 0 (it reached t_end) costs nothing: its warps return at once.
-struct BatchProblem {
-    long long offset;      // element offset of the problem's planes in each buffer
-    int nx, ny;
-    double x0, y0, dx, dy;
-    double rx, ry;         // 1/dx, 1/dy (host)
-    int n_strips, n_segs;
-    int warp0;             // first task / reduction slot of the problem
-};
 
-template <class T, int K, int B, int PHYS>
+template <class T, int K, int B, int PHYS, bool LIM = true>
 __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, const BatchProblem* __restrict__ probs,
                                                            const int2* __restrict__ tasks, int n_tasks,
                                                            DevState* states, int* curs, unsigned* done,
@@ -1334,7 +1328,7 @@ __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, con
     pv.ds_ = ds;
     pv.cur_ = curs + tk.x;
     pv.done_ = done;
-    step2d_body<T, K, B, PHYS>(a, pv, tk.y);
+    step2d_body<T, K, B, PHYS, false, false, LIM>(a, pv, tk.y);
 }
 
 }  // namespace crk

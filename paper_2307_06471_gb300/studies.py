@@ -202,7 +202,7 @@ def vortex(sizes=(80, 160, 320), T=10.0, precision="f32", cfl=0.1):
             "rows": rows}
 
 
-def ensemble(n=256, steps=40, precision="f32", seed=20230713, autotune=True):
+def ensemble(n=256, steps=40, precision="f32", seed=20230713, autotune=True, limit_mode="pass"):
     import torch
     import crkdg_inputs as inp
     from paper_2307_06471_gb300 import binding as B
@@ -216,6 +216,7 @@ def ensemble(n=256, steps=40, precision="f32", seed=20230713, autotune=True):
                  stream=stream.cuda_stream)
     for i, e in enumerate(ens):
         bt.project_function(i, lambda X, Y: inp.riemann_ic(X, Y, e["prim"]))
+    bt.set_limit_mode(B.LIMIT_PASS if limit_mode == "pass" else B.LIMIT_FUSED)
     bt.limit(50.0)
     bt.positivity(1e-10)
     tuned = bt.autotune(0.16) if autotune else None
@@ -228,7 +229,8 @@ def ensemble(n=256, steps=40, precision="f32", seed=20230713, autotune=True):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     stat = [bt.info(i) for i in range(n)]
-    out = {"study": "ensemble", "precision": precision, "problems": n, "total_cells": bt.total_cells,
+    out = {"study": "ensemble", "precision": precision, "limit_mode": limit_mode, "problems": n,
+           "total_cells": bt.total_cells,
            "dof": bt.total_cells * 24, "steps": steps, "ms_per_step": ms / steps,
            "dof_updates_per_s": bt.total_cells * 24 * steps / (ms * 1e-3), "tasks": bt.n_tasks,
            "autotune_us": tuned, "nonzero_status": sum(1 for s in stat if s[2]),
@@ -625,6 +627,7 @@ if __name__ == "__main__":
     ap.add_argument("--T", type=float, default=10.0)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--limit-mode", default="pass", choices=["pass", "fused"])
     a = ap.parse_args()
     if a.study == "vortex":
         r = vortex(tuple(int(x) for x in a.sizes.split(",")), a.T, a.precision)
@@ -649,5 +652,5 @@ if __name__ == "__main__":
     elif a.study == "dmr_full":
         r = dmr_full(*(int(v) for v in a.sizes.split(",")[:3])) if a.sizes != "80,160,320" else dmr_full()
     else:
-        r = ensemble(a.n, a.steps, a.precision)
+        r = ensemble(a.n, a.steps, a.precision, limit_mode=a.limit_mode)
     print(json.dumps(r, default=float))
