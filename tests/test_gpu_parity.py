@@ -244,6 +244,42 @@ def test_limit_pass_equals_fused_limit(prec):
     assert min(a[2]) > 0
 
 
+def test_fp32_reductions_match_the_oracle():
+    """The FP32 path's FP64 reductions against the oracle's, on a state whose
+    values are exactly FP32 (so that only summation order separates them):
+    crkdg_conservation (totals sum_K |K| ubar_K, eq. (3.4)) and crkdg_cfl_dt
+    (cfl / max_K (s_x/dx + s_y/dy)) to 1e-13 relative; and the wave speed
+    that a step's own epilogue reduces in FP32 from the new averages (the
+    device dt of the next step) against the oracle's FP64 maximum over the
+    same new state, to FP32 rounding (2e-6)."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    nx, ny = 83, 47
+    gs, dg = make_pair_2d(nx, ny, (0, 2.0, 0, 1.0), 2, "P", "euler", "ssprk3", PER, "f32")
+    u = inp.random_modal_state(ny, nx, 2, "P", "euler", seed=21)
+    u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
+    gs.set_state(to_planes(u), 0.0)
+    tot = gs.conservation()
+    want = dg.total(u)
+    assert np.allclose(tot, want, rtol=1e-13, atol=0)
+    dt = gs.cfl_dt(0.4)
+    assert dt == pytest.approx(cfl_dt_2d(dg, u, 0.4), rel=1e-13)
+    # one device-driven step: its epilogue's FP32 wave speed of the new state
+    stream = torch.cuda.Stream()
+    g = B.Solver(gs.mesh, 2, B.BASIS_P, GTB.SSPRK3, B.EULER, B.F32, stream=stream.cuda_stream)
+    g.set_state(to_planes(u), 0.0)
+    g.advance(1, 0.4, 10.0)
+    buf = torch.zeros(5, dtype=torch.float64, pin_memory=True)
+    g.run_state_async(buf.data_ptr())
+    assert g.sync() == (0, 0)
+    new = from_planes(g.get_state())
+    assert buf[4].item() == pytest.approx(dg.max_speed(new), rel=2e-6)
+    assert np.allclose(g.conservation(), dg.total(new), rtol=1e-13, atol=0)
+    g.close()
+    gs.close()
+
+
 def test_run_state_async_follows_device_driven_steps():
     """crkdg_run_state_async copies {t, dt, t_end, cfl, max wave speed} of the
     device run state into pinned host memory in stream order: after each
