@@ -382,6 +382,12 @@ int crkdg_mlp_train(crkdg_mlp* m, const float* X_dev, const float* y_dev, int n,
                     double pos_weight, unsigned long long seed, double* last_epoch_loss);
 /* logits_dev[n] from X_dev[n][40] (tensor-core inference) */
 int crkdg_mlp_predict(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev);
+/* The same logits on the fifth-generation tensor cores (tcgen05): tiles of
+ * 512 samples per block, each layer four M = 128 products with BF16
+ * operands in shared memory and the FP32 accumulators in tensor memory.  Its waits for
+ * the tensor core are bounded: CRKDG_ETIMEOUT (logits NaN) if one runs out.
+ * Synchronises. */
+int crkdg_mlp_predict_tc(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev);
 const char* crkdg_mlp_last_error(void);
 /* features X_dev[cell][40] and TVB labels y_dev[cell] (1 = the TVB-minmod
  * test with parameter M flags the cell) of the context's stored state */
@@ -391,6 +397,15 @@ int crkdg_features(crkdg_ctx* ctx, float* X_dev, float* y_dev, double M_tvb);
  * reconstruction is always the TVB-minmod one).  net = NULL: TVB test only.
  * 2D Euler, k = 2, FP32; net must outlive its use. */
 int crkdg_set_indicator(crkdg_ctx* ctx, const crkdg_mlp* net, double z_lo, double z_hi);
+/* Which tensor-core path evaluates the network in the limiter pass (the
+ * default limit mode): CRKDG_MLP_TCGEN05 (default) tiles of 512 cells per
+ * block, each layer four tcgen05 products of 128 rows with the accumulators
+ * in tensor memory (a bounded wait that runs out leaves the TVB test deciding
+ * and sets CRKDG_ST_TIMEOUT for crkdg_sync); CRKDG_MLP_MMA_SYNC one warp per
+ * 32 cells with mma.sync.  The indicator fused into the step's load always uses
+ * mma.sync.  EINVAL for another value. */
+enum { CRKDG_MLP_TCGEN05 = 0, CRKDG_MLP_MMA_SYNC = 1 };
+int crkdg_set_indicator_engine(crkdg_ctx* ctx, int engine);
 
 /* Measured arithmetic peak of the current device (no counterpart in the
  * paper: the denominator of the step kernel's roofline, which is bound by

@@ -24,6 +24,7 @@ ADVECTION, EULER = 0, 1
 BASIS_P, BASIS_Q = 0, 1
 F32, F64, F32C, F32D = 0, 1, 2, 3
 LIMIT_FUSED, LIMIT_PASS = 0, 1
+MLP_TCGEN05, MLP_MMA_SYNC = 0, 1
 FORM_QUADRATURE, FORM_AUTO = 0, 1
 FLUX_LLF = 0
 ST_NONPHYSICAL, ST_NAN, ST_TIMEOUT = 1, 2, 4
@@ -119,6 +120,8 @@ _SIGS = {
     "crkdg_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                   C.c_double, C.c_ulonglong, C.POINTER(C.c_double)]),
     "crkdg_mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "crkdg_mlp_predict_tc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "crkdg_set_indicator_engine": (C.c_int, [C.c_void_p, C.c_int]),
     "crkdg_mlp_last_error": (C.c_char_p, []),
     "crkdg_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]),
     "crkdg_set_indicator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
@@ -331,6 +334,9 @@ class Solver:
     def set_limit_mode(self, mode):
         _check(lib().crkdg_set_limit_mode(self.ctx, int(mode)))
 
+    def set_indicator_engine(self, engine):
+        _check(lib().crkdg_set_indicator_engine(self.ctx, int(engine)))
+
     def get_limit_mode(self):
         m = C.c_int()
         _check(lib().crkdg_get_limit_mode(self.ctx, C.byref(m)))
@@ -536,3 +542,7 @@ class MLP:
 
     def predict(self, X_ptr, n, out_ptr):
         _mcheck(lib().crkdg_mlp_predict(self.ptr, C.c_void_p(X_ptr), int(n), C.c_void_p(out_ptr)))
+
+    def predict_tc(self, X_ptr, n, out_ptr):
+        """The logits on the tcgen05 tensor cores (tiles of 512 samples)."""
+        _mcheck(lib().crkdg_mlp_predict_tc(self.ptr, C.c_void_p(X_ptr), int(n), C.c_void_p(out_ptr)))

@@ -78,6 +78,7 @@ struct crkdg_ctx {
     double* d_tab_fe = nullptr;   // forward-Euler tableau (RKDG stages)
     const float* mlp = nullptr;   // learned indicator parameters (device), owned by a crkdg_mlp
     float mlp_zlo = 0.f, mlp_zhi = 0.f;
+    int mlp_engine = CRKDG_MLP_TCGEN05;   // crkdg_set_indicator_engine (the limiter pass's inference)
     int limit_mode = CRKDG_LIMIT_PASS;   // where a pending limit runs (crkdg_set_limit_mode)
     double* d_stage = nullptr;            // FP64 staging of state I/O for FP32 states (first use)
     int op_form = CRKDG_FORM_AUTO;        // crkdg_set_operator_form
@@ -236,7 +237,10 @@ int enqueue_limit_pass(crkdg_ctx* c, double M, int dt_from_dev) {
         a.mlp = c->mlp;
         a.mlp_zlo = c->mlp_zlo;
         a.mlp_zhi = c->mlp_zhi;
-        CK(crk::limit2d_euler_f32_mlp(c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count, c->stream));
+        if (c->mlp_engine == CRKDG_MLP_TCGEN05)
+            CK(crk::limit2d_euler_f32_mlp_tc(c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count, c->stream));
+        else
+            CK(crk::limit2d_euler_f32_mlp(c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count, c->stream));
         return CRKDG_OK;
     }
     CK(crk::launch_limit2d(c->kphys, c->precision, c->k, c->basis, a, c->u[c->cur], &c->d_state->lim_count,
@@ -837,6 +841,16 @@ int crkdg_set_indicator(crkdg_ctx* c, const crkdg_mlp* net, double z_lo, double 
     c->mlp = crkdg_mlp_device_params(net);
     c->mlp_zlo = (float)z_lo;
     c->mlp_zhi = (float)z_hi;
+    return CRKDG_OK;
+}
+
+int crkdg_set_indicator_engine(crkdg_ctx* c, int engine) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (engine != CRKDG_MLP_TCGEN05 && engine != CRKDG_MLP_MMA_SYNC)
+        return fail(CRKDG_EINVAL, "unknown indicator engine");
+    c->mlp_engine = engine;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
     return CRKDG_OK;
 }
 

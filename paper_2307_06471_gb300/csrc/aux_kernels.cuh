@@ -4,6 +4,7 @@
 #pragma once
 #include "common.cuh"
 #include "limiter.cuh"
+#include "mlp_tc.cuh"
 #include "mlp_warp.cuh"
 
 // resident blocks per SM the limiter pass is compiled for (tuning knob)
@@ -152,10 +153,13 @@ __global__ void project1d_kernel(const double* __restrict__ vals, T* __restrict_
 // run state when the run is device driven.  (x, y): the thread's cell; lanes
 // past the east side (x >= nx) take part in the shuffles (and, with MLPI, in
 // the warp's network evaluation) and limit nothing.
-// MLPI: the troubled-cell decision comes from the learned indicator (limit
-// if the logit exceeds zhi, keep if it is below zlo, TVB test in between),
-// evaluated for the warp's 32 cells with the weights mw and the warp's
-// staging area.
+// MLPK: where the troubled-cell decision comes from.  0: the TVB test.  1
+// and 2: the learned indicator (limit if the logit exceeds zhi, keep if it is
+// below zlo, TVB test in between), evaluated for the warp's 32 cells with
+// mma.sync (1: weights mw, the warp's staging area) or for the block's 128
+// cells on the tcgen05 tensor cores (2: tcs, its barrier phase; *tc_ok turns
+// false, for the whole block, once a bounded wait ran out, and the TVB test
+// decides from then on).
 // The mesh a limiter pass works on: a single problem's (from the launch
 // arguments) or one problem of a batch (from its table entry), the time of
 // its ghost data (tsrc: the device run state, or null for a.t) and its TVB
@@ -167,9 +171,10 @@ struct LimMesh {
     double Mdx2, Mdy2;
 };
 
-template <class T, int K, int B, int PHYS, bool MLPI>
+template <class T, int K, int B, int PHYS, int MLPK>
 __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g, T* __restrict__ u, int x, int y,
-                                             const MlpSmem* mw, __nv_bfloat16* stage) {
+                                             const MlpSmem* mw, __nv_bfloat16* stage, MlpTcSmem* tcs = nullptr,
+                                             uint32_t* phase = nullptr, bool* tc_ok = nullptr) {
     constexpr int NM = Tab2D<K, B>::NM;
     constexpr int NV = Phys<T, PHYS>::NV;
     const int nx = g.nx, ny = g.ny;
@@ -227,12 +232,19 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g
         if (!pery && y == ny - 1) ghost(3, x, ny, nbN);
     }
     int mode = -1;
-    if constexpr (MLPI) {
-        // every lane of the warp takes part (lanes past the side on a copy
-        // of the last cell); features of the cell and its four neighbours
+    if constexpr (MLPK != 0) {
+        // every lane of the warp (MLPK 2: of the block) takes part (lanes
+        // past the side on a copy of the last cell); features of the cell and
+        // its four neighbours
         float feat[MLP_IN];
         mlp_features<T, NM>(c, nbE, nbW, nbN, nbS, a.mlp_scale, feat);
-        const float z = mlp_warp_logit(*mw, feat, stage);
+        float z;
+        if constexpr (MLPK == 1) {
+            z = mlp_warp_logit(*mw, feat, stage);
+        } else {
+            z = __int_as_float(0x7fc00000);   // NaN: neither band, the TVB test decides
+            if (*tc_ok) *tc_ok = mlp_tc_logit(*tcs, feat, *phase, z);   // block-uniform
+        }
         mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
     }
     bool fl = false;
@@ -282,7 +294,7 @@ template <class T, int K, int B, int PHYS>
 __global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
                                                                       unsigned long long* flag_count) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool fl = limit2d_cell<T, K, B, PHYS, false>(a, single_mesh<T>(a), u, x, blockIdx.y, nullptr, nullptr);
+    const bool fl = limit2d_cell<T, K, B, PHYS, 0>(a, single_mesh<T>(a), u, x, blockIdx.y, nullptr, nullptr);
     const unsigned b = __ballot_sync(0xffffffffu, fl);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(flag_count, (unsigned long long)__popc(b));
 }
@@ -309,10 +321,40 @@ __global__ void __launch_bounds__(LIMIT_MLP_THREADS) limit2d_mlp_kernel(const St
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int y = (int)(tile / xt);
         const int x = (int)(tile % xt) * LIMIT_MLP_THREADS + threadIdx.x;
-        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, true>(a, g, u, x, y, &mw, stage);
+        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, 1>(a, g, u, x, y, &mw, stage);
         cnt += __popc(__ballot_sync(0xffffffffu, fl));
     }
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(flag_count, (unsigned long long)cnt);
+}
+
+// The same pass with the network on the tcgen05 tensor cores (mlp_tc.cuh):
+// blocks of 512 threads, one tile of 512 cells of a row per iteration
+// (grid-stride), each tile's network four M = 128 products per layer.  Each
+// block holds the BF16 weights in shared memory and its accumulator columns
+// of tensor memory for its whole walk.  A bounded wait that runs out makes
+// the TVB test decide for the rest of the block's walk and sets ST_TIMEOUT
+// in the run state.
+template <class T, int K, int B>
+__global__ void __launch_bounds__(MLPTC_CELLS) limit2d_mlp_tc_kernel(const StepArgs a, T* __restrict__ u,
+                                                                 unsigned long long* flag_count) {
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    MlpTcSmem& tcs = *reinterpret_cast<MlpTcSmem*>(smem_tc);
+    mlp_tc_setup(tcs, a.mlp);
+    const LimMesh g = single_mesh<T>(a);
+    const int xt = (a.nx + MLPTC_CELLS - 1) / MLPTC_CELLS;
+    const long long tiles = (long long)xt * a.ny;
+    uint32_t phase = 0;
+    bool tc_ok = true;
+    unsigned cnt = 0;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int y = (int)(tile / xt);
+        const int x = (int)(tile % xt) * MLPTC_CELLS + threadIdx.x;
+        const bool fl = limit2d_cell<T, K, B, PHYS_EULER, 2>(a, g, u, x, y, nullptr, nullptr, &tcs, &phase, &tc_ok);
+        cnt += __popc(__ballot_sync(0xffffffffu, fl));
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(flag_count, (unsigned long long)cnt);
+    if (!tc_ok && threadIdx.x == 0) atomicOr(&a.ds->status, ST_TIMEOUT);
+    mlp_tc_teardown(tcs);
 }
 
 // The limiter pass of a batched ensemble: one block of 128 threads per row
@@ -340,7 +382,7 @@ __global__ void __launch_bounds__(128, CRK_LIMIT_MINB)
     const double mx2 = a.M * pb.dx * pb.dx, my2 = a.M * pb.dy * pb.dy;
     g.Mdx2 = sizeof(T) == 4 ? double(float(mx2)) : mx2;
     g.Mdy2 = sizeof(T) == 4 ? double(float(my2)) : my2;
-    const bool fl = limit2d_cell<T, K, B, PHYS_EULER, false>(a, g, u, rt.z + threadIdx.x, rt.y, nullptr, nullptr);
+    const bool fl = limit2d_cell<T, K, B, PHYS_EULER, 0>(a, g, u, rt.z + threadIdx.x, rt.y, nullptr, nullptr);
     const unsigned b = __ballot_sync(0xffffffffu, fl);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(&ds->lim_count, (unsigned long long)__popc(b));
 }

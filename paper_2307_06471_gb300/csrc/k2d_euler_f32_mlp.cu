@@ -52,7 +52,35 @@ cudaError_t run_limit_mlp(const StepArgs& a, void* u, unsigned long long* flags,
     return cudaGetLastError();
 }
 
+template <int B>
+cudaError_t run_limit_mlp_tc(const StepArgs& a, void* u, unsigned long long* flags, cudaStream_t st) {
+    auto kern = limit2d_mlp_tc_kernel<float, 2, B>;
+    const size_t smem = sizeof(MlpTcSmem) + MLPTC_SMEM_SLACK;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int per_sm = 1;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MLPTC_CELLS, smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    // resident blocks only (each holds its tensor-memory columns for its walk)
+    const int blocks_sm = std::max(1, std::min(per_sm, 512 / MLPTC_TMEM_COLS));
+    const int grid = blocks_sm * std::max(1, sm_count());
+    StepArgs b = a;
+    set_derived(b);
+    kern<<<grid, MLPTC_CELLS, smem, st>>>(b, static_cast<float*>(u), flags);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t limit2d_euler_f32_mlp_tc(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
+                                     cudaStream_t st) {
+    if (k != 2) return cudaErrorInvalidValue;
+    return basis == 0 ? run_limit_mlp_tc<0>(a, u, flags, st) : run_limit_mlp_tc<1>(a, u, flags, st);
+}
 
 cudaError_t limit2d_euler_f32_mlp(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
                                   cudaStream_t st) {

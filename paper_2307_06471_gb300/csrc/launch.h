@@ -70,6 +70,9 @@ cudaError_t info2d_euler_f32d(int k, int basis, int s, KernelInfo* info);
 cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
 cudaError_t limit2d_euler_f32_mlp(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
                                   cudaStream_t st);
+// the pass with the network on the tcgen05 tensor cores
+cudaError_t limit2d_euler_f32_mlp_tc(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
+                                     cudaStream_t st);
 
 // out = alpha x + beta y (n elements of the state precision), and DevState.t = t
 cudaError_t launch_axpby(int prec, void* out, const void* x, const void* y, double alpha, double beta, size_t n,

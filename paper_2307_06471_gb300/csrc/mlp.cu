@@ -4,6 +4,7 @@
 // solver state.  C ABI part of include/crkdg.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -11,7 +12,9 @@
 
 #include "../../include/crkdg.h"
 #include "aux_kernels.cuh"
+#include "launch.h"
 #include "mlp_warp.cuh"
+#include "mlp_tc.cuh"
 
 using crk::MLP_H;
 using crk::MLP_IN;
@@ -188,6 +191,29 @@ __global__ void __launch_bounds__(128) mlp_predict_kernel(const float* __restric
     if (s < n) logits[s] = z;
 }
 
+// The same inference on the fifth-generation tensor cores (mlp_tc.cuh): one
+// tile of 128 samples per block iteration, grid-stride over the tiles; a
+// bounded wait that ran out sets ST_TIMEOUT in *status.
+__global__ void __launch_bounds__(crk::MLPTC_CELLS) mlp_predict_tc_kernel(const float* __restrict__ prm,
+                                                             const float* __restrict__ X, int n,
+                                                             float* __restrict__ logits, unsigned* status) {
+    extern __shared__ __align__(1024) unsigned char smt[];
+    crk::MlpTcSmem& s = *reinterpret_cast<crk::MlpTcSmem*>(smt);
+    crk::mlp_tc_setup(s, prm);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && (long long)tile * crk::MLPTC_CELLS < n; tile += gridDim.x) {
+        const int i = tile * crk::MLPTC_CELLS + threadIdx.x;
+        float f[MLP_IN];
+        for (int k = 0; k < MLP_IN; ++k) f[k] = i < n ? X[(size_t)i * MLP_IN + k] : 0.f;
+        float z;
+        ok = crk::mlp_tc_logit(s, f, phase, z);
+        if (i < n) logits[i] = z;
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(status, crk::ST_TIMEOUT);
+    crk::mlp_tc_teardown(s);
+}
+
 // Features and TVB labels of every cell of a P^2 2D Euler state (one thread
 // per cell).  Label 1 when the TVB-minmod test of the limiter flags the cell.
 template <class T, int K, int B>
@@ -243,6 +269,7 @@ double uniform01(uint64_t& s) { return ((splitmix(s) >> 11) + 0.5) * (1.0 / 9007
 }  // namespace
 
 struct crkdg_mlp {
+    unsigned* d_status = nullptr;   // ST_TIMEOUT of a tensor-core wait that ran out
     float* d_prm = nullptr;
     float* d_m = nullptr;
     float* d_v = nullptr;
@@ -281,6 +308,11 @@ int crkdg_mlp_create(unsigned long long seed, void* stream, crkdg_mlp** out) {
         crkdg_mlp_destroy(m);
         return mfail(CRKDG_ENOMEM, "cudaMalloc failed");
     }
+    if (cudaMalloc(&m->d_status, sizeof(unsigned)) != cudaSuccess) {
+        crkdg_mlp_destroy(m);
+        return mfail(CRKDG_ENOMEM, "cudaMalloc failed");
+    }
+    cudaMemset(m->d_status, 0, sizeof(unsigned));
     cudaMemcpy(m->d_prm, h.data(), MLP_NPARAM * 4, cudaMemcpyHostToDevice);
     cudaMemset(m->d_m, 0, MLP_NPARAM * 4);
     cudaMemset(m->d_v, 0, MLP_NPARAM * 4);
@@ -293,6 +325,7 @@ void crkdg_mlp_destroy(crkdg_mlp* m) {
     cudaStreamSynchronize(m->stream);
     for (float* p : {m->d_prm, m->d_m, m->d_v, m->d_grad})
         if (p) cudaFree(p);
+    if (m->d_status) cudaFree(m->d_status);
     delete m;
 }
 
@@ -406,6 +439,22 @@ int crkdg_mlp_predict(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev
     mlp_predict_kernel<<<(n + 127) / 128, 128, smem, m->stream>>>(m->d_prm, X_dev, n, logits_dev);
     MCK(cudaGetLastError());
     MCK(cudaStreamSynchronize(m->stream));
+    return CRKDG_OK;
+}
+
+int crkdg_mlp_predict_tc(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev) {
+    if (!m || !X_dev || !logits_dev || n < 1) return mfail(CRKDG_EINVAL, "bad argument");
+    const size_t smem = sizeof(crk::MlpTcSmem) + crk::MLPTC_SMEM_SLACK;
+    MCK(cudaFuncSetAttribute(mlp_predict_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long tiles = ((long long)n + crk::MLPTC_CELLS - 1) / crk::MLPTC_CELLS;
+    const int grid = (int)std::min<long long>(tiles, 4LL * std::max(1, crk::sm_count()));
+    MCK(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), m->stream));
+    mlp_predict_tc_kernel<<<grid, crk::MLPTC_CELLS, smem, m->stream>>>(m->d_prm, X_dev, n, logits_dev, m->d_status);
+    MCK(cudaGetLastError());
+    unsigned st = 0;
+    MCK(cudaMemcpyAsync(&st, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, m->stream));
+    MCK(cudaStreamSynchronize(m->stream));
+    if (st) return mfail(CRKDG_ETIMEOUT, "a bounded wait for the tensor core ran out");
     return CRKDG_OK;
 }
 

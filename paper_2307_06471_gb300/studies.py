@@ -349,11 +349,17 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
     nx, ny = perf_n
     # (the network in the limiter pass, the default limit mode, and fused
     # into the step's load)
-    for name, prec, use_net, fused in (("f32_tvb", B.F32, False, False), ("f32_mlp", B.F32, True, False),
-                                       ("f32_mlp_fused", B.F32, True, True), ("f64_tvb", B.F64, False, False)):
+    # (the network in the limiter pass on the tcgen05 tensor cores -- the
+    # default -- or with mma.sync, and fused into the step's load)
+    for name, prec, use_net, fused, mma in (("f32_tvb", B.F32, False, False, False),
+                                            ("f32_mlp", B.F32, True, False, False),
+                                            ("f32_mlp_pass_mma_sync", B.F32, True, False, True),
+                                            ("f32_mlp_fused", B.F32, True, True, True),
+                                            ("f64_tvb", B.F64, False, False, False)):
         s = _shock_vortex_solver(B, GTB, inp, nx, ny, prec, sh)
         if use_net:
             s.set_indicator(net)
+            s.set_indicator_engine(B.MLP_MMA_SYNC if mma else B.MLP_TCGEN05)
         if fused:
             s.set_limit_mode(B.LIMIT_FUSED)
         n_steps = perf_steps if prec == B.F32 else max(5, perf_steps // 10)

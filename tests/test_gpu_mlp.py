@@ -111,6 +111,37 @@ def test_bf16_inference_matches_oracle_forward():
     net.close()
 
 
+def test_tcgen05_inference_matches_mma_sync_and_oracle():
+    """The fifth-generation tensor-core inference (tiles of 512 samples,
+    tcgen05 products into tensor memory) against the mma.sync inference on
+    the same BF16 network (same BF16 roundings of weights and activations;
+    only the FP32 accumulation order differs) and against the FP64 oracle
+    forward with the BF16 bands of the test above; 1000 samples (a partial
+    last tile) and one sample."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    rng = np.random.default_rng(16)
+    P = omlp.init_params(rng)
+    vec = _oracle_params(P)
+    net = B.MLP(seed=1)
+    net.set_params(vec)
+    for n in (1000, 1):
+        Xh = rng.normal(size=(n, 40)).astype(np.float32)
+        X = torch.tensor(Xh, device="cuda")
+        a = torch.zeros(n, dtype=torch.float32, device="cuda")
+        b = torch.full((n,), -7.0, dtype=torch.float32, device="cuda")
+        net.predict(X.data_ptr(), n, a.data_ptr())
+        net.predict_tc(X.data_ptr(), n, b.data_ptr())
+        za, zb = a.cpu().numpy(), b.cpu().numpy()
+        z, _ = omlp.forward(_unpack(vec), Xh.astype(np.float64))
+        scale = max(1.0, np.max(np.abs(z)))
+        assert np.all(np.isfinite(zb))
+        assert np.max(np.abs(zb - za)) < 0.02 * scale
+        assert np.max(np.abs(zb - z)) < 0.05 * scale
+        assert np.mean(np.abs(zb - z)) < 0.01 * scale
+    net.close()
+
+
 def test_training_learns_a_separable_rule():
     import torch
     from paper_2307_06471_gb300 import binding as B
@@ -130,17 +161,19 @@ def test_training_learns_a_separable_rule():
     net.close()
 
 
-@pytest.mark.parametrize("where", ["fused", "pass"])
+@pytest.mark.parametrize("where", ["fused", "pass_tcgen05", "pass_mma_sync"])
 @pytest.mark.parametrize("mode", ["always", "never", "tvb_band"])
 def test_fused_indicator_decisions(mode, where):
     """A network whose output is a constant logit forces the decision (all
     cells limited / none); a band covering every logit leaves it to TVB.  The
-    indicator runs fused into the step's load or in the limiter pass."""
+    indicator runs fused into the step's load (mma.sync) or in the limiter
+    pass (tcgen05 or mma.sync); nx = 300 leaves a partial tile."""
     import torch
     from paper_2307_06471_gb300 import binding as B
-    nx, ny, M = 64, 40, 20.0
+    nx, ny, M = 300, 40, 20.0
     gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), 2, "P", "euler", "ssprk3", OUT, "f32")
     gs.set_limit_mode(B.LIMIT_FUSED if where == "fused" else B.LIMIT_PASS)
+    gs.set_indicator_engine(B.MLP_MMA_SYNC if where == "pass_mma_sync" else B.MLP_TCGEN05)
     u = _state(nx, ny, seed=42)
     u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
     vec = np.zeros(11009, dtype=np.float32)
@@ -164,4 +197,5 @@ def test_fused_indicator_decisions(mode, where):
         lim = tvb_limit(dg, u, M, 0.0, force=force)[0]
     want = tvb_limit(dg, crkdg_step(dg, lim, 0.0, dt, OTB.SSPRK3), M, dt)[0]
     assert rel_err(got, want) < 2e-5
+    assert gs.sync() == (0, 0)    # no bounded wait ran out
     net.close()
