@@ -381,6 +381,45 @@ def learned(n_train_members=200, snapshots=3, steps_between=40, epochs=6, eval_n
     return out
 
 
+def indicator_rates(N=2048, steps=30, seed=5):
+    """Device time per step of the shock-vortex problem (P^2, SSP-RK3, FP32,
+    N x N) with the TVB test and with a network (seeded, untrained, logit
+    band [-2, 2] so that both the network and the TVB fallback decide) in the
+    limiter pass on the tcgen05 tensor cores, in the pass with mma.sync, and
+    fused into the step's load; `steps` device-driven steps between CUDA
+    events after 3 warm-up steps."""
+    import torch
+    import crkdg_inputs as inp
+    from paper_2307_06471_gb300 import binding as B
+    from paper_2307_06471_gb300 import tableaux as GTB
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    net = B.MLP(seed=seed, stream=sh)
+    out = {"study": "indicator_rates", "mesh": "%dx%d" % (N, N), "steps": steps}
+    for name, use, engine, fused in (("tvb", False, None, False), ("pass_tcgen05", True, B.MLP_TCGEN05, False),
+                                     ("pass_mma_sync", True, B.MLP_MMA_SYNC, False), ("fused_mma_sync", True, None, True)):
+        s = _shock_vortex_solver(B, GTB, inp, N, N, B.F32, sh)
+        if use:
+            s.set_indicator(net, -2.0, 2.0)
+        if engine is not None:
+            s.set_indicator_engine(engine)
+        if fused:
+            s.set_limit_mode(B.LIMIT_FUSED)
+        s.advance(3, 0.16, 10.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s.step_device()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["ms_per_step_" + name] = e0.elapsed_time(e1) / steps
+        out["status_" + name] = s.sync()[1]
+        s.close()
+    net.close()
+    return out
+
+
 def compact(nx=1920, ny=480, steps=100, precision="f32"):
     """cRKDG (limiter pass + one fused step launch) against the original RKDG (SSP-RK3
     in Shu--Osher form, limiter after every stage) on the double Mach
@@ -627,7 +666,8 @@ def build_lib():
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["vortex", "ensemble", "learned", "compact", "advection1d", "advection2d",
-                                     "advection_hbm", "dmr_full", "precision_rates", "matched_l1"])
+                                     "advection_hbm", "dmr_full", "precision_rates", "matched_l1",
+                                     "indicator_rates"])
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--sizes", default="80,160,320")
     ap.add_argument("--T", type=float, default=10.0)
@@ -652,6 +692,9 @@ if __name__ == "__main__":
         r = precision_rates(int(a.sizes.split(",")[0]) if a.sizes != "80,160,320" else 1280, a.steps,
                             variants=tuple(a.precision.split(",")) if a.precision != "f32" else
                             ("f32", "f32c", "f32d", "f64"))
+    elif a.study == "indicator_rates":   # --sizes N --steps K
+        build_lib()
+        r = indicator_rates(int(a.sizes.split(",")[0]) if a.sizes != "80,160,320" else 2048, a.steps)
     elif a.study == "matched_l1":
         build_lib()
         r = matched_l1(T=a.T if a.T != 10.0 else 1.0)
