@@ -171,6 +171,57 @@ struct LimMesh {
     double Mdx2, Mdy2;
 };
 
+// Ghost averages beyond the non-periodic sides for cell (x, y) of the mesh
+// (its own average `own` gives the exterior state where the boundary
+// condition wants it); the loaded neighbour averages there are replaced.
+template <class T, int NV>
+__device__ __forceinline__ void limit2d_ghosts(const StepArgs& a, const LimMesh& g, int x, int y, const T* own,
+                                               T* nbW, T* nbE, T* nbS, T* nbN) {
+    const bool perx = a.bc[0].type == BC_PERIODIC, pery = a.bc[2].type == BC_PERIODIC;
+    // ghost average beyond a non-periodic side (cx, cy: the ghost cell)
+    auto ghost = [&](int side, int cx, int cy, T* out) {
+        cold_branch();
+        const int cxc = opaque(cx), cyc = opaque(cy);
+        bc_exterior<T, NV>(a.bc[side], side < 2 ? 0 : 1, own, [&](double& xg, double& yg, double& tg) {
+            xg = g.x0 + (cxc + 0.5) * g.dx;
+            yg = g.y0 + (cyc + 0.5) * g.dy;
+            tg = g.tsrc ? g.tsrc->t : a.t;
+        }, out);
+    };
+    if (!perx && x == 0) ghost(0, -1, y, nbW);
+    if (!perx && x == g.nx - 1) ghost(1, g.nx, y, nbE);
+    if (!pery && y == 0) ghost(2, x, -1, nbS);
+    if (!pery && y == g.ny - 1) ghost(3, x, g.ny, nbN);
+}
+
+// TVB-minmod test and limit (mode: -1 the test decides, 0 keep, 1 limit),
+// then the positivity scaling, of cell (x, y) with modes c and neighbour
+// averages nb*; modes 1.. of a changed cell are written back to u.  Returns
+// whether the cell was troubled.
+template <class T, int K, int B, int NV, int NM>
+__device__ __forceinline__ bool limit2d_apply(const StepArgs& a, const LimMesh& g, T* __restrict__ u, int x, int y,
+                                              T (&c)[NV][NM], const T* nbW, const T* nbE, const T* nbS,
+                                              const T* nbN, int mode) {
+    const size_t plane = (size_t)g.nx * g.ny;
+    const T Mdx2 = T(g.Mdx2), Mdy2 = T(g.Mdy2);
+    T gam, ppe;
+    if constexpr (sizeof(T) == 4) {
+        gam = a.gammaf; ppe = a.pp_epsf;
+    } else {
+        gam = a.gamma; ppe = a.pp_eps;
+    }
+    bool fl = false;
+    if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam, mode);
+    bool sc = false;
+    if (a.pp_on) sc = positivity_cell<T, NV, NM, K, B>(c, gam, ppe);
+    if (fl || sc)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * g.nx + x] = c[v][m];
+    return fl;
+}
+
 template <class T, int K, int B, int PHYS, int MLPK>
 __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g, T* __restrict__ u, int x, int y,
                                              const MlpSmem* mw, __nv_bfloat16* stage, MlpTcSmem* tcs = nullptr,
@@ -215,22 +266,7 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g
         if (needW) nbW[v] = ldW[v];
         if (needE) nbE[v] = ldE[v];
     }
-    // ghost average beyond a non-periodic side (cx, cy: the ghost cell)
-    auto ghost = [&](int side, int cx, int cy, T* out) {
-        cold_branch();
-        const int cxc = opaque(cx), cyc = opaque(cy);
-        bc_exterior<T, NV>(a.bc[side], side < 2 ? 0 : 1, own, [&](double& xg, double& yg, double& tg) {
-            xg = g.x0 + (cxc + 0.5) * g.dx;
-            yg = g.y0 + (cyc + 0.5) * g.dy;
-            tg = g.tsrc ? g.tsrc->t : a.t;
-        }, out);
-    };
-    if (inside) {
-        if (!perx && x == 0) ghost(0, -1, y, nbW);
-        if (!perx && x == nx - 1) ghost(1, nx, y, nbE);
-        if (!pery && y == 0) ghost(2, x, -1, nbS);
-        if (!pery && y == ny - 1) ghost(3, x, ny, nbN);
-    }
+    if (inside) limit2d_ghosts<T, NV>(a, g, x, y, own, nbW, nbE, nbS, nbN);
     int mode = -1;
     if constexpr (MLPK != 0) {
         // every lane of the warp (MLPK 2: of the block) takes part (lanes
@@ -247,25 +283,7 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g
         }
         mode = z > a.mlp_zhi ? 1 : (z < a.mlp_zlo ? 0 : -1);
     }
-    bool fl = false;
-    if (inside) {
-        const T Mdx2 = T(g.Mdx2), Mdy2 = T(g.Mdy2);
-        T gam, ppe;
-        if constexpr (sizeof(T) == 4) {
-            gam = a.gammaf; ppe = a.pp_epsf;
-        } else {
-            gam = a.gamma; ppe = a.pp_eps;
-        }
-        if (a.tvb_on) fl = tvb_limit_cell<T, NV, NM>(c, nbW, nbE, nbS, nbN, Mdx2, Mdy2, gam, mode);
-        bool sc = false;
-        if (a.pp_on) sc = positivity_cell<T, NV, NM, K, B>(c, gam, ppe);
-        if (fl || sc)
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int m = 1; m < NM; ++m) u[(size_t)(v * NM + m) * plane + (size_t)y * nx + x] = c[v][m];
-    }
-    return fl;
+    return inside ? limit2d_apply<T, K, B, NV, NM>(a, g, u, x, y, c, nbW, nbE, nbS, nbN, mode) : false;
 }
 
 // the mesh view of a single-problem launch: thresholds as set_limiter_params

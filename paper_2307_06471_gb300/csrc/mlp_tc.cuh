@@ -25,6 +25,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "mlp_warp.cuh"
 
@@ -55,6 +56,15 @@ struct __align__(128) MlpTcSmem {
 // element index of (row, k) in a [rows x K] operand of the core-matrix layout
 __host__ __device__ constexpr int tc_idx(int row, int k, int K) {
     return ((row >> 3) * (K >> 3) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// two FP32 values rounded to BF16 (round to nearest even), packed: x0 in the
+// low half
+__device__ __forceinline__ uint32_t bf16x2_bits(float x0, float x1) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(x0, x1);
+    uint32_t u;
+    memcpy(&u, &b, sizeof u);
+    return u;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -202,14 +212,20 @@ __device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s, const float* bias) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) tc_ld16(lane_addr + 16 * q, r[q]);
     tc_ld_wait();
+    // one 16-byte store per core matrix: the eight rows of a warp's row
+    // group fill the core matrix's 128 bytes, one shared-memory wavefront
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-            const int c = 16 * q + j;
-            const float x0 = fmaxf(__uint_as_float(r[q][j]) + bias[c], 0.f);
-            const float x1 = fmaxf(__uint_as_float(r[q][j + 1]) + bias[c + 1], 0.f);
-            *reinterpret_cast<__nv_bfloat162*>(&s.act[tc_idx(row, c, MLP_H)]) = __floats2bfloat162_rn(x0, x1);
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = 16 * q + 8 * h + 2 * j;
+                w[j] = bf16x2_bits(fmaxf(__uint_as_float(r[q][8 * h + 2 * j]) + bias[c], 0.f),
+                                   fmaxf(__uint_as_float(r[q][8 * h + 2 * j + 1]) + bias[c + 1], 0.f));
+            }
+            *reinterpret_cast<uint4*>(&s.act[tc_idx(row, 16 * q + 8 * h, MLP_H)]) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     fence_async_smem();
     tc_fence_before();
@@ -223,9 +239,14 @@ __device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s, const float* bias) {
 __device__ __forceinline__ bool mlp_tc_logit(MlpTcSmem& s, const float* feat, uint32_t& phase, float& z) {
     const int row = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < MLP_INP; k += 2)
-        *reinterpret_cast<__nv_bfloat162*>(&s.act[tc_idx(row, k, MLP_INP)]) =
-            __floats2bfloat162_rn(k < MLP_IN ? feat[k] : 0.f, k + 1 < MLP_IN ? feat[k + 1] : 0.f);
+    for (int k = 0; k < MLP_INP; k += 8) {    // 16 bytes (one core-matrix row) per store
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w[j] = bf16x2_bits(k + 2 * j < MLP_IN ? feat[k + 2 * j] : 0.f,
+                               k + 2 * j + 1 < MLP_IN ? feat[k + 2 * j + 1] : 0.f);
+        *reinterpret_cast<uint4*>(&s.act[tc_idx(row, k, MLP_INP)]) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();

@@ -137,3 +137,36 @@ def rel_err(a, b, vaxis=-2):
     floor = 1e-2 * max(1.0, float(np.max(np.abs(b))))
     return max(float(np.max(np.abs(a[v] - b[v]))) / max(float(np.max(np.abs(b[v]))), floor)
                for v in range(b.shape[0]))
+
+
+def tvb_margin(dg, u, t, M, cells):
+    """Smallest distance of a TVB-minmod decision of the listed patch cells
+    from a tie, relative to the size of the compared numbers.  Per cell,
+    direction and characteristic field (the oracle's reading: a1 the slope
+    mode, a2/a3 the forward/backward average differences, projected with the
+    left eigenvectors at the cell average) the decision flips where
+    |a1| = M h^2 (the TVB threshold) or, above it, where |a1| equals the
+    smaller of |a2|, |a3| with all signs equal (minmod returns a1 itself:
+    not troubled, else troubled).  Each distance is divided by the largest
+    magnitude entering it, the sum of |L_fj| |u_j| over the projected
+    vector."""
+    from oracle.limiter import neighbour_averages
+    avg = u[..., 0]
+    nb = neighbour_averages(dg, avg, t)
+    best = np.inf
+    for (cy, cx) in cells:
+        ab = avg[cy, cx]
+        for axis, (m, hi, lo, h) in enumerate(((1, "E", "W", dg.dx), (2, "N", "S", dg.dy))):
+            L = np.linalg.inv(dg.phys.right_eigenvectors(ab, axis))
+            vecs = (u[cy, cx, :, m], nb[hi][cy, cx] - ab, ab - nb[lo][cy, cx])
+            a = [L @ v for v in vecs]
+            scale = [np.abs(L) @ np.abs(v) for v in vecs]
+            thr = M * h * h
+            for f in range(4):
+                best = min(best, abs(abs(a[0][f]) - thr) / max(thr, scale[0][f], 1e-300))
+                same = np.sign(a[1][f]) == np.sign(a[0][f]) == np.sign(a[2][f])
+                if abs(a[0][f]) > thr and same:
+                    other = min(abs(a[1][f]), abs(a[2][f]))
+                    sc = max(scale[0][f], scale[1][f], scale[2][f], 1e-300)
+                    best = min(best, abs(abs(a[0][f]) - other) / sc)
+    return best

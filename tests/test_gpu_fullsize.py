@@ -14,7 +14,7 @@ from oracle import tableaux as OTB
 from oracle.dg2d import DG2D, crkdg_step
 from oracle.limiter import positivity_limit, tvb_limit
 from oracle.physics import Euler
-from tests.pairing import oracle_bc
+from tests.pairing import oracle_bc, tvb_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -34,43 +34,10 @@ def _bcs():
             "N": ("dmr_top", post, pre, st["x0"], st["slope"], st["xspeed"])}
 
 
-def _tvb_margin(dg, u, t, M, cells):
-    """Smallest distance of a TVB-minmod decision of the listed patch cells
-    from a tie, relative to the size of the compared numbers.  Per cell,
-    direction and characteristic field (the oracle's reading: a1 the slope
-    mode, a2/a3 the forward/backward average differences, projected with the
-    left eigenvectors at the cell average) the decision flips where
-    |a1| = M h^2 (the TVB threshold) or, above it, where |a1| equals the
-    smaller of |a2|, |a3| with all signs equal (minmod returns a1 itself:
-    not troubled, else troubled).  Each distance is divided by the largest
-    magnitude entering it, the sum of |L_fj| |u_j| over the projected
-    vector."""
-    from oracle.limiter import neighbour_averages
-    avg = u[..., 0]
-    nb = neighbour_averages(dg, avg, t)
-    best = np.inf
-    for (cy, cx) in cells:
-        ab = avg[cy, cx]
-        for axis, (m, hi, lo, h) in enumerate(((1, "E", "W", dg.dx), (2, "N", "S", dg.dy))):
-            L = np.linalg.inv(dg.phys.right_eigenvectors(ab, axis))
-            vecs = (u[cy, cx, :, m], nb[hi][cy, cx] - ab, ab - nb[lo][cy, cx])
-            a = [L @ v for v in vecs]
-            scale = [np.abs(L) @ np.abs(v) for v in vecs]
-            thr = M * h * h
-            for f in range(4):
-                best = min(best, abs(abs(a[0][f]) - thr) / max(thr, scale[0][f], 1e-300))
-                same = np.sign(a[1][f]) == np.sign(a[0][f]) == np.sign(a[2][f])
-                if abs(a[0][f]) > thr and same:
-                    other = min(abs(a[1][f]), abs(a[2][f]))
-                    sc = max(scale[0][f], scale[1][f], scale[2][f], 1e-300)
-                    best = min(best, abs(abs(a[0][f]) - other) / sc)
-    return best
-
-
 def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10, margins=False):
     """u: full state [y, x, v, m] (FP64 values of the GPU input); returns the
     oracle's limited u^{n+1} of cell (y, x) and, with margins, the tie
-    margin (_tvb_margin) of every limiter decision the cell depends on: the
+    margin (tvb_margin) of every limiter decision the cell depends on: the
     limit of u^n in the cell and its four neighbours, and the limit of
     u^{n+1} in the cell."""
     dx, dy = (BOX[1] - BOX[0]) / NX, (BOX[3] - BOX[2]) / NY
@@ -89,9 +56,9 @@ def _oracle_cell(u, y, x, t0, dt, M=50.0, eps=1e-10, margins=False):
     cy, cx = y - ya, x - xa
     near = [(cy + j, cx + i) for (j, i) in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1))
             if 0 <= cy + j < yb - ya and 0 <= cx + i < xb - xa]
-    m_n = _tvb_margin(dg, p, t0, M, near)
+    m_n = tvb_margin(dg, p, t0, M, near)
     w_raw = crkdg_step(dg, lim(p, t0), t0, dt, OTB.SSPRK3)
-    m_n1 = _tvb_margin(dg, w_raw, t0 + dt, M, [(cy, cx)])
+    m_n1 = tvb_margin(dg, w_raw, t0 + dt, M, [(cy, cx)])
     return w[y - ya, x - xa], min(m_n, m_n1)
 
 
