@@ -6,11 +6,14 @@
 // weights (BF16, shared memory), FP32 accumulators in tensor memory
 // (columns 64 j .. 64 j + 63 for the tile's cells 128 j .. 128 j + 127) --
 // issued by one thread and committed to one barrier; every thread then
-// reads its cell's row of the accumulator (tcgen05.ld), adds the bias,
-// applies ReLU and writes the row back to shared memory, BF16, as the next
-// layer's A operand.  Four products per round trip through the barrier:
-// measured 2.43 ms per 2048^2 shock-vortex step with one (128 cells), 1.64
-// with two, 1.46 with four.
+// reads its cell's row of the accumulator (tcgen05.ld), applies ReLU while
+// rounding it to BF16 (one cvt.relu per pair) and writes the row back to
+// shared memory as the next layer's A operand.  The biases ride in the
+// products: every A operand carries a column of ones (column 40 of the
+// input layer's K = 48, column 64 of the hidden layers' K = 80) against a
+// weight column holding the bias (in BF16).  Four products per round trip
+// through the barrier: measured 2.43 ms per 2048^2 shock-vortex step with
+// one (128 cells), 1.64 with two, 1.46 with four.
 //
 // Shared-memory operands use the tensor core's K-major layout without
 // swizzling: 8 x 8 BF16 core matrices of 128 contiguous bytes (8 rows of 16
@@ -40,17 +43,19 @@ constexpr int MLPTC_TMEM_COLS = 64 * MLPTC_NT;
 // dynamic shared memory of a CTA beyond the operands
 constexpr size_t MLPTC_SMEM_SLACK = 0;
 constexpr unsigned MLPTC_WAIT_LIMIT = 1u << 22;
+// K of the hidden and output layers' products: 64 activations, a column of
+// ones (the bias) and 15 zero columns
+constexpr int MLPTC_KH = MLP_H + 16;
 
 struct __align__(128) MlpTcSmem {
-    __nv_bfloat16 act[MLPTC_CELLS * MLP_H];  // A operands: K = 48 (layer 1) or 64
-    __nv_bfloat16 W1[MLP_H * MLP_INP];       // B operands: N x K
-    __nv_bfloat16 W2[MLP_H * MLP_H];
-    __nv_bfloat16 W3[MLP_H * MLP_H];
-    __nv_bfloat16 W4[16 * MLP_H];            // output row 0, rows 1..15 zero
-    float b1[MLP_H], b2[MLP_H], b3[MLP_H];
-    float b4;
-    unsigned tmem;                           // tensor-memory address from tcgen05.alloc
-    unsigned long long bar;                  // completion barrier of the products
+    __nv_bfloat16 act1[MLPTC_CELLS * MLP_INP];   // input layer's A: 40 features, 1, zeros (K = 48)
+    __nv_bfloat16 acth[MLPTC_CELLS * MLPTC_KH];  // hidden layers' A: 64 activations, 1, zeros (K = 80)
+    __nv_bfloat16 W1[MLP_H * MLP_INP];           // B operands: N x K, the bias in the ones column
+    __nv_bfloat16 W2[MLP_H * MLPTC_KH];
+    __nv_bfloat16 W3[MLP_H * MLPTC_KH];
+    __nv_bfloat16 W4[16 * MLPTC_KH];             // output row 0, rows 1..15 zero
+    unsigned tmem;                               // tensor-memory address from tcgen05.alloc
+    unsigned long long bar;                      // completion barrier of the products
 };
 
 // element index of (row, k) in a [rows x K] operand of the core-matrix layout
@@ -64,6 +69,13 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float x0, float x1) {
     const __nv_bfloat162 b = __floats2bfloat162_rn(x0, x1);
     uint32_t u;
     memcpy(&u, &b, sizeof u);
+    return u;
+}
+// ReLU of two FP32 values rounded to BF16 (max(x, 0), round to nearest
+// even) in one conversion, packed: x0 in the low half
+__device__ __forceinline__ uint32_t bf16x2_relu_bits(float x0, float x1) {
+    uint32_t u;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(x1), "f"(x0));
     return u;
 }
 
@@ -160,35 +172,40 @@ __device__ __forceinline__ void mlp_tc_setup(MlpTcSmem& s, const float* __restri
     }
     for (int i = threadIdx.x; i < MLP_H * MLP_INP; i += blockDim.x) {
         const int n = i / MLP_INP, k = i % MLP_INP;
-        s.W1[tc_idx(n, k, MLP_INP)] = __float2bfloat16_rn(k < MLP_IN ? W1[n * MLP_IN + k] : 0.f);
+        const float w = k < MLP_IN ? W1[n * MLP_IN + k] : (k == MLP_IN ? b1[n] : 0.f);
+        s.W1[tc_idx(n, k, MLP_INP)] = __float2bfloat16_rn(w);
     }
-    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) {
-        const int n = i / MLP_H, k = i % MLP_H;
-        s.W2[tc_idx(n, k, MLP_H)] = __float2bfloat16_rn(W2[i]);
-        s.W3[tc_idx(n, k, MLP_H)] = __float2bfloat16_rn(W3[i]);
+    for (int i = threadIdx.x; i < MLP_H * MLPTC_KH; i += blockDim.x) {
+        const int n = i / MLPTC_KH, k = i % MLPTC_KH;
+        const bool wk = k < MLP_H, bk = k == MLP_H;
+        s.W2[tc_idx(n, k, MLPTC_KH)] = __float2bfloat16_rn(wk ? W2[n * MLP_H + k] : (bk ? b2[n] : 0.f));
+        s.W3[tc_idx(n, k, MLPTC_KH)] = __float2bfloat16_rn(wk ? W3[n * MLP_H + k] : (bk ? b3[n] : 0.f));
     }
-    for (int i = threadIdx.x; i < 16 * MLP_H; i += blockDim.x) {
-        const int n = i / MLP_H, k = i % MLP_H;
-        s.W4[tc_idx(n, k, MLP_H)] = __float2bfloat16_rn(n == 0 ? W4[k] : 0.f);
+    for (int i = threadIdx.x; i < 16 * MLPTC_KH; i += blockDim.x) {
+        const int n = i / MLPTC_KH, k = i % MLPTC_KH;
+        const float w = n != 0 ? 0.f : (k < MLP_H ? W4[k] : (k == MLP_H ? b4[0] : 0.f));
+        s.W4[tc_idx(n, k, MLPTC_KH)] = __float2bfloat16_rn(w);
     }
-    for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) {
-        s.b1[i] = b1[i];
-        s.b2[i] = b2[i];
-        s.b3[i] = b3[i];
+    // the hidden layers' ones and zero columns (64 .. 79), written once: the
+    // epilogues write columns 0 .. 63 only
+    for (int r = threadIdx.x; r < MLPTC_CELLS; r += blockDim.x) {
+        *reinterpret_cast<uint4*>(&s.acth[tc_idx(r, MLP_H, MLPTC_KH)]) = make_uint4(bf16x2_bits(1.f, 0.f), 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(&s.acth[tc_idx(r, MLP_H + 8, MLPTC_KH)]) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (threadIdx.x == 0) s.b4 = b4[0];
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
 }
 
-// One layer: thread 0 issues acc = act [128 x K] * W^T [K x N] into tensor
-// memory and commits to the barrier; every thread waits (bounded).
-__device__ __forceinline__ bool mlp_tc_layer(MlpTcSmem& s, const __nv_bfloat16* W, int K, int N, uint32_t& phase) {
+// One layer: thread 0 issues acc = A [128 x K] * W^T [K x N] into tensor
+// memory for each of the tile's row blocks and commits to the barrier; every
+// thread waits (bounded).
+__device__ __forceinline__ bool mlp_tc_layer(MlpTcSmem& s, const __nv_bfloat16* A, const __nv_bfloat16* W, int K,
+                                             int N, uint32_t& phase) {
     const uint32_t bar = smem_u32(&s.bar);
     if (threadIdx.x == 0) {
-        const uint32_t a0 = smem_u32(s.act), b0 = smem_u32(W);
+        const uint32_t a0 = smem_u32(A), b0 = smem_u32(W);
         const uint32_t idesc = tc_idesc(MLPTC_M, N);
         for (int rb = 0; rb < MLPTC_NT; ++rb)      // rows 128 rb ..: 128 K BF16 further, accumulator columns + 64 rb
             for (int ks = 0; ks < K / 16; ++ks)    // K = 16 per product: two core matrices along K
@@ -203,30 +220,34 @@ __device__ __forceinline__ bool mlp_tc_layer(MlpTcSmem& s, const __nv_bfloat16* 
     return ok;
 }
 
-// ReLU(acc + bias) of this thread's row -> BF16 row of the next A operand
-// (K = 64), then make the writes visible to the tensor core
-__device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s, const float* bias) {
+// ReLU(acc) of this thread's row (the bias is in acc) -> BF16 columns 0 .. 63
+// of its row of the next A operand, then make the writes visible to the
+// tensor core
+__device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s) {
     const int row = threadIdx.x;
     const uint32_t lane_addr = tc_row_addr(s.tmem, row);
-    uint32_t r[4][16];   // the row's 64 accumulator columns, four loads in flight
+    // the row's 64 accumulator columns in two halves of two loads in flight;
+    // one 16-byte store per core matrix: the eight rows of a warp's row group
+    // fill the core matrix's 128 bytes, one shared-memory wavefront
 #pragma unroll
-    for (int q = 0; q < 4; ++q) tc_ld16(lane_addr + 16 * q, r[q]);
-    tc_ld_wait();
-    // one 16-byte store per core matrix: the eight rows of a warp's row
-    // group fill the core matrix's 128 bytes, one shared-memory wavefront
+    for (int half = 0; half < 2; ++half) {
+        uint32_t r[2][16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 2; ++q) tc_ld16(lane_addr + 32 * half + 16 * q, r[q]);
+        tc_ld_wait();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t w[4];
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = 16 * q + 8 * h + 2 * j;
-                w[j] = bf16x2_bits(fmaxf(__uint_as_float(r[q][8 * h + 2 * j]) + bias[c], 0.f),
-                                   fmaxf(__uint_as_float(r[q][8 * h + 2 * j + 1]) + bias[c + 1], 0.f));
+            for (int h = 0; h < 2; ++h) {
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    w[j] = bf16x2_relu_bits(__uint_as_float(r[q][8 * h + 2 * j]),
+                                            __uint_as_float(r[q][8 * h + 2 * j + 1]));
+                *reinterpret_cast<uint4*>(&s.acth[tc_idx(row, 32 * half + 16 * q + 8 * h, MLPTC_KH)]) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
-            *reinterpret_cast<uint4*>(&s.act[tc_idx(row, 16 * q + 8 * h, MLP_H)]) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -242,27 +263,29 @@ __device__ __forceinline__ bool mlp_tc_logit(MlpTcSmem& s, const float* feat, ui
     for (int k = 0; k < MLP_INP; k += 8) {    // 16 bytes (one core-matrix row) per store
         uint32_t w[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            w[j] = bf16x2_bits(k + 2 * j < MLP_IN ? feat[k + 2 * j] : 0.f,
-                               k + 2 * j + 1 < MLP_IN ? feat[k + 2 * j + 1] : 0.f);
-        *reinterpret_cast<uint4*>(&s.act[tc_idx(row, k, MLP_INP)]) = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int j = 0; j < 4; ++j) {
+            const int k0 = k + 2 * j;   // features, then the ones column (the bias), then zeros
+            w[j] = bf16x2_bits(k0 < MLP_IN ? feat[k0] : (k0 == MLP_IN ? 1.f : 0.f),
+                               k0 + 1 < MLP_IN ? feat[k0 + 1] : 0.f);
+        }
+        *reinterpret_cast<uint4*>(&s.act1[tc_idx(row, k, MLP_INP)]) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     z = __int_as_float(0x7fc00000);
-    if (!mlp_tc_layer(s, s.W1, MLP_INP, MLP_H, phase)) return false;
-    mlp_tc_hidden(s, s.b1);
-    if (!mlp_tc_layer(s, s.W2, MLP_H, MLP_H, phase)) return false;
-    mlp_tc_hidden(s, s.b2);
-    if (!mlp_tc_layer(s, s.W3, MLP_H, MLP_H, phase)) return false;
-    mlp_tc_hidden(s, s.b3);
-    if (!mlp_tc_layer(s, s.W4, MLP_H, 16, phase)) return false;
+    if (!mlp_tc_layer(s, s.act1, s.W1, MLP_INP, MLP_H, phase)) return false;
+    mlp_tc_hidden(s);
+    if (!mlp_tc_layer(s, s.acth, s.W2, MLPTC_KH, MLP_H, phase)) return false;
+    mlp_tc_hidden(s);
+    if (!mlp_tc_layer(s, s.acth, s.W3, MLPTC_KH, MLP_H, phase)) return false;
+    mlp_tc_hidden(s);
+    if (!mlp_tc_layer(s, s.acth, s.W4, MLPTC_KH, 16, phase)) return false;
     uint32_t v[16];
     tc_ld16(tc_row_addr(s.tmem, row), v);
     tc_ld_wait();
-    z = __uint_as_float(v[0]) + s.b4;
+    z = __uint_as_float(v[0]);
     // the accumulator is read before the tile's next product overwrites it
     tc_fence_before();
     __syncthreads();
