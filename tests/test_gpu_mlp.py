@@ -199,3 +199,50 @@ def test_fused_indicator_decisions(mode, where):
     assert rel_err(got, want) < 2e-5
     assert gs.sync() == (0, 0)    # no bounded wait ran out
     net.close()
+
+
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_pass_decisions_follow_the_network_logits(engine):
+    """A seeded untrained network whose logits spread over both signs, with
+    the band [z_lo, z_hi] between the 30 % and 70 % quantiles of the logits:
+    the limiter pass (tcgen05 or mma.sync inference) limits a cell when its
+    logit, from the same features by the separate mma.sync inference, is
+    above z_hi, keeps it when below z_lo, and leaves the TVB test to decide
+    in between.  A cell may differ from that only where its logit lies
+    within 2 % of the logit scale of a band edge (BF16 rounding and the
+    accumulation order)."""
+    import torch
+    from paper_2307_06471_gb300 import binding as B
+    nx, ny, M = 300, 40, 20.0
+    gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), 2, "P", "euler", "ssprk3", OUT, "f32")
+    gs.set_indicator_engine(B.MLP_TCGEN05 if engine == "tcgen05" else B.MLP_MMA_SYNC)
+    u = _state(nx, ny, seed=43)
+    u = from_planes(to_planes(u).astype(np.float32).astype(np.float64))
+    gs.set_state(to_planes(u), 0.0)
+    n = nx * ny
+    X = torch.zeros(n, 40, dtype=torch.float32, device="cuda")
+    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    gs.features(X.data_ptr(), y.data_ptr(), M)
+    net = B.MLP(seed=5)
+    zt = torch.zeros(n, dtype=torch.float32, device="cuda")
+    net.predict(X.data_ptr(), n, zt.data_ptr())
+    z = zt.cpu().numpy().astype(np.float64).reshape(ny, nx)
+    z_lo, z_hi = np.quantile(z, 0.3), np.quantile(z, 0.7)
+    assert z_lo < z_hi
+    gs.set_indicator(net, z_lo, z_hi)
+    gs.limit(M)
+    gs.apply_limit()
+    got = from_planes(gs.get_state())
+    assert gs.sync() == (0, 0)
+    tvb_flags = tvb_limit(dg, u, M, 0.0)[1]
+    decide = np.where(z > z_hi, True, np.where(z < z_lo, False, tvb_flags))
+    want = tvb_limit(dg, u, M, 0.0, force=decide)[0]
+    # the decisions matter: forcing changes the outcome against plain TVB
+    assert np.count_nonzero(decide != tvb_flags) > 0.05 * n
+    scale = np.max(np.abs(want), axis=(0, 1, 3))
+    bad = np.any(np.abs(got - want) > 2e-5 * scale[None, None, :, None], axis=(2, 3))
+    zs = max(1.0, float(np.max(np.abs(z))))
+    near = (np.abs(z - z_hi) < 0.02 * zs) | (np.abs(z - z_lo) < 0.02 * zs)
+    assert not np.any(bad & ~near), np.argwhere(bad & ~near)[:5]
+    assert np.count_nonzero(bad) <= 0.01 * n
+    net.close()
