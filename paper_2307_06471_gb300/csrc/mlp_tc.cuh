@@ -43,6 +43,12 @@ constexpr int MLPTC_TMEM_COLS = 64 * MLPTC_NT;
 // dynamic shared memory of a CTA beyond the operands
 constexpr size_t MLPTC_SMEM_SLACK = 0;
 constexpr unsigned MLPTC_WAIT_LIMIT = 1u << 22;
+// tensor-memory loads (16 columns each) in flight per wait in the epilogue:
+// 1, 2 or 4 (tuning knob)
+#ifndef MLPTC_LD
+#define MLPTC_LD 2
+#endif
+static_assert(MLPTC_LD == 1 || MLPTC_LD == 2 || MLPTC_LD == 4, "MLPTC_LD divides 4");
 // K of the hidden and output layers' products: 64 activations, a column of
 // ones (the bias) and 15 zero columns
 constexpr int MLPTC_KH = MLP_H + 16;
@@ -226,17 +232,19 @@ __device__ __forceinline__ bool mlp_tc_layer(MlpTcSmem& s, const __nv_bfloat16* 
 __device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s) {
     const int row = threadIdx.x;
     const uint32_t lane_addr = tc_row_addr(s.tmem, row);
-    // the row's 64 accumulator columns in two halves of two loads in flight;
-    // one 16-byte store per core matrix: the eight rows of a warp's row group
-    // fill the core matrix's 128 bytes, one shared-memory wavefront
+    // the row's 64 accumulator columns in groups of MLPTC_LD loads of 16
+    // columns in flight; one 16-byte store per core matrix: the eight rows of
+    // a warp's row group fill the core matrix's 128 bytes, one shared-memory
+    // wavefront
+    constexpr int G = MLPTC_LD;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        uint32_t r[2][16];
+    for (int half = 0; half < 4 / G; ++half) {
+        uint32_t r[G][16];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) tc_ld16(lane_addr + 32 * half + 16 * q, r[q]);
+        for (int q = 0; q < G; ++q) tc_ld16(lane_addr + 16 * G * half + 16 * q, r[q]);
         tc_ld_wait();
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < G; ++q)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t w[4];
@@ -244,7 +252,7 @@ __device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& s) {
                 for (int j = 0; j < 4; ++j)
                     w[j] = bf16x2_relu_bits(__uint_as_float(r[q][8 * h + 2 * j]),
                                             __uint_as_float(r[q][8 * h + 2 * j + 1]));
-                *reinterpret_cast<uint4*>(&s.acth[tc_idx(row, 32 * half + 16 * q + 8 * h, MLPTC_KH)]) =
+                *reinterpret_cast<uint4*>(&s.acth[tc_idx(row, 16 * G * half + 16 * q + 8 * h, MLPTC_KH)]) =
                     make_uint4(w[0], w[1], w[2], w[3]);
             }
     }
