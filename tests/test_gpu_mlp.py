@@ -201,8 +201,8 @@ def test_fused_indicator_decisions(mode, where):
     net.close()
 
 
-@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
-def test_pass_decisions_follow_the_network_logits(engine):
+@pytest.mark.parametrize("engine,nx", [("tcgen05", 300), ("tcgen05", 298), ("mma_sync", 300)])
+def test_pass_decisions_follow_the_network_logits(engine, nx):
     """A seeded untrained network whose logits spread over both signs, with
     the band [z_lo, z_hi] between the 30 % and 70 % quantiles of the logits:
     the limiter pass (tcgen05 or mma.sync inference) limits a cell when its
@@ -210,10 +210,11 @@ def test_pass_decisions_follow_the_network_logits(engine):
     above z_hi, keeps it when below z_lo, and leaves the TVB test to decide
     in between.  A cell may differ from that only where its logit lies
     within 2 % of the logit scale of a band edge (BF16 rounding and the
-    accumulation order)."""
+    accumulation order).  nx = 300 and 298: a partial last tile of 512 and
+    of 32 cells, rows of 16-byte multiples and not."""
     import torch
     from paper_2307_06471_gb300 import binding as B
-    nx, ny, M = 300, 40, 20.0
+    ny, M = 40, 20.0
     gs, dg = make_pair_2d(nx, ny, (0, 1.0, 0, 1.0), 2, "P", "euler", "ssprk3", OUT, "f32")
     gs.set_indicator_engine(B.MLP_TCGEN05 if engine == "tcgen05" else B.MLP_MMA_SYNC)
     u = _state(nx, ny, seed=43)
