@@ -150,7 +150,12 @@ int max_wpb(crkdg_ctx* c) {
 
 // Segment rows for which the step kernel's warps fill the resident slots of
 // the device's SMs `waves` times over (registers and private shared memory of the
-// kernel decide the slots; blocks of w warps), segments of >= 8 rows.
+// kernel decide the slots; blocks of w warps), segments of >= 1 row.  On a
+// mesh too small to fill the slots the segments get short: a warp marches
+// through its rows one after another, so the step takes about (rows + 2)
+// row times however few warps run (the vortex Q^2 RK4 step at 80^2 took
+// 2.94 ms in FP64 and 0.185 ms in the deviation form with 8-row segments,
+// 0.78 and 0.052 ms with 1-row segments).
 int wave_rows(crkdg_ctx* c, int w, int waves, int* rows) {
     const int ns = (c->mesh.nx + 29) / 30;
     crk::KernelInfo ki;
@@ -162,7 +167,7 @@ int wave_rows(crkdg_ctx* c, int w, int waves, int* rows) {
     resident = std::max(w, resident / w * w);
     const long target = (long)std::max(1, crk::sm_count()) * resident * waves;
     const long nseg = std::max(1L, target / ns);
-    int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
+    int L = (int)std::max(1L, ((long)c->mesh.ny + nseg - 1) / nseg);
     *rows = std::min(L, c->mesh.ny);
     return CRKDG_OK;
 }
@@ -205,7 +210,7 @@ bool use_linear(const crkdg_ctx* c) {
 }
 
 // one wave of the modal step: as many warps as its registers and shared
-// memory let the device's SMs hold, segments of >= 8 rows
+// memory let the device's SMs hold, segments of >= 1 row
 int linear_shape(crkdg_ctx* c) {
     if (c->lin_seg_rows > 0) return CRKDG_OK;
     crk::KernelInfo ki;
@@ -218,7 +223,7 @@ int linear_shape(crkdg_ctx* c) {
     resident = std::max(wpb, resident / wpb * wpb);
     const int ns = (c->mesh.nx + 29) / 30;
     const long nseg = std::max(1L, (long)std::max(1, crk::sm_count()) * resident / ns);
-    const int L = (int)std::max(8L, ((long)c->mesh.ny + nseg - 1) / nseg);
+    const int L = (int)std::max(1L, ((long)c->mesh.ny + nseg - 1) / nseg);
     c->lin_seg_rows = std::min(L, c->mesh.ny);
     c->lin_wpb = wpb;
     return CRKDG_OK;
