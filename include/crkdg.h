@@ -384,9 +384,12 @@ int crkdg_mlp_train(crkdg_mlp* m, const float* X_dev, const float* y_dev, int n,
 int crkdg_mlp_predict(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev);
 /* The same logits on the fifth-generation tensor cores (tcgen05): tiles of
  * 512 samples per block, each layer four M = 128 products with BF16
- * operands in shared memory and the FP32 accumulators in tensor memory.  Its waits for
- * the tensor core are bounded: CRKDG_ETIMEOUT (logits NaN) if one runs out.
- * Synchronises. */
+ * operands in shared memory and the FP32 accumulators in tensor memory.  The
+ * biases enter the products in BF16 (a ones column of the activations against
+ * a bias column of the weights; crkdg_mlp_predict adds them in FP32), so the
+ * two agree to BF16 rounding of the biases and the accumulation order.  Its
+ * waits for the tensor core are bounded: CRKDG_ETIMEOUT (logits NaN) if one
+ * runs out.  Synchronises. */
 int crkdg_mlp_predict_tc(crkdg_mlp* m, const float* X_dev, int n, float* logits_dev);
 const char* crkdg_mlp_last_error(void);
 /* features X_dev[cell][40] and TVB labels y_dev[cell] (1 = the TVB-minmod
