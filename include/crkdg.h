@@ -39,6 +39,8 @@
 #ifndef CRKDG_H
 #define CRKDG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -137,6 +139,32 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
                  double gamma, int physics, int precision, const double* phys_params,
                  void* stream, crkdg_ctx** out);
 void crkdg_destroy(crkdg_ctx* ctx);
+
+/* Bytes of one copy of the state of the context crkdg_create makes for these
+ * arguments: cells x variables x modes values of 4 bytes (CRKDG_F32,
+ * CRKDG_F32C / CRKDG_F32D twice: hi planes then lo planes) or 8 (CRKDG_F64),
+ * laid out as planes [v][m][y][x].  Host arithmetic only.  EINVAL for a
+ * null pointer or arguments crkdg_create rejects as out of range. */
+int crkdg_state_bytes(const crkdg_mesh* mesh, int k, int basis, int physics, int precision, size_t* bytes);
+
+/* crkdg_create with the state's two ping-pong copies in device memory the
+ * caller owns (for example two PyTorch tensors): state_a and state_b each
+ * hold crkdg_state_bytes bytes on the current device, 16-byte aligned and
+ * not overlapping, and stay allocated until crkdg_destroy, which does not
+ * free them.  The context reads and writes them on its stream only; the
+ * state starts as the contents of state_a at t = 0 (nothing is zeroed).
+ * Each step writes the other copy: crkdg_current_state says which holds the
+ * current state.  EINVAL for null, misaligned, overlapping or non-device
+ * buffers; otherwise as crkdg_create. */
+int crkdg_create_on_buffers(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab,
+                            double gamma, int physics, int precision, const double* phys_params, void* stream,
+                            void* state_a, void* state_b, crkdg_ctx** out);
+
+/* The copy that holds the current state -- which = 0 (state_a, the first
+ * copy) or 1 -- and its device address, as of the calls made so far (work
+ * queued on the stream included): read it after synchronising the stream.
+ * A pending limit (crkdg_limit) is not yet applied to it. */
+int crkdg_current_state(const crkdg_ctx* ctx, int* which, void** dev_ptr);
 
 /* Sizes: cells = nx*ny, modes per cell, variables, volume points per cell. */
 int crkdg_sizes(const crkdg_ctx* ctx, int* n_cells, int* n_modes, int* n_vars, int* n_qp);

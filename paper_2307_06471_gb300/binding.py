@@ -53,6 +53,11 @@ _SIGS = {
     "crkdg_create": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.POINTER(Tableau), C.c_double,
                                C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_void_p)]),
     "crkdg_destroy": (None, [C.c_void_p]),
+    "crkdg_state_bytes": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "crkdg_create_on_buffers": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.POINTER(Tableau),
+                                          C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "crkdg_current_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_void_p)]),
     "crkdg_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 4),
     "crkdg_quadrature_points": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "crkdg_project_ic": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -197,17 +202,35 @@ def make_mesh(dim, nx, ny, box, bc, bc_fn=(0, 0, 0, 0), bc_params=None):
     return m
 
 
+def state_bytes(mesh, k, basis, physics, precision):
+    """Bytes of one copy of the state (crkdg_state_bytes)."""
+    n = C.c_size_t()
+    _check(lib().crkdg_state_bytes(C.byref(mesh), int(k), int(basis), int(physics), int(precision), C.byref(n)))
+    return n.value
+
+
 class Solver:
     """One cRKDG context.  State arrays are FP64 numpy planes [v, m, y, x]."""
 
-    def __init__(self, mesh, k, basis, tableau, physics, precision, gamma=1.4, beta=(1.0, 0.0), stream=None):
+    def __init__(self, mesh, k, basis, tableau, physics, precision, gamma=1.4, beta=(1.0, 0.0), stream=None,
+                 state_buffers=None):
+        """state_buffers: None (the context allocates its state) or two
+        caller-owned device addresses (ints, e.g. torch data_ptr()) of
+        state_bytes(...) bytes each (crkdg_create_on_buffers)."""
         L = lib()
         self.ctx = C.c_void_p()
         pp = np.asarray(beta, dtype=np.float64)
         self._pp = pp
         tab = make_tableau(*tableau) if not isinstance(tableau, Tableau) else tableau
-        _check(L.crkdg_create(C.byref(mesh), k, basis, FLUX_LLF, C.byref(tab), gamma, physics, precision,
-                              _dptr(pp), C.c_void_p(stream) if stream else None, C.byref(self.ctx)))
+        st = C.c_void_p(stream) if stream else None
+        if state_buffers is None:
+            _check(L.crkdg_create(C.byref(mesh), k, basis, FLUX_LLF, C.byref(tab), gamma, physics, precision,
+                                  _dptr(pp), st, C.byref(self.ctx)))
+        else:
+            a, b = state_buffers
+            _check(L.crkdg_create_on_buffers(C.byref(mesh), k, basis, FLUX_LLF, C.byref(tab), gamma, physics,
+                                             precision, _dptr(pp), st, C.c_void_p(int(a)), C.c_void_p(int(b)),
+                                             C.byref(self.ctx)))
         self.mesh = mesh
         self.config = {"k": k, "basis": basis, "stages": tab.s, "physics": physics, "precision": precision}
         nc, nm, nv, nq = C.c_int(), C.c_int(), C.c_int(), C.c_int()
@@ -219,6 +242,12 @@ class Solver:
         if self.ctx:
             lib().crkdg_destroy(self.ctx)
             self.ctx = C.c_void_p()
+
+    def current_state(self):
+        """(which copy, device address) of the current state (crkdg_current_state)."""
+        w, p = C.c_int(), C.c_void_p()
+        _check(lib().crkdg_current_state(self.ctx, C.byref(w), C.byref(p)))
+        return w.value, p.value or 0
 
     def __del__(self):
         try:

@@ -83,6 +83,7 @@ struct crkdg_ctx {
     double* d_stage = nullptr;            // FP64 staging of state I/O for FP32 states (first use)
     int op_form = CRKDG_FORM_AUTO;        // crkdg_set_operator_form
     int lin_seg_rows = 0, lin_wpb = 0;    // launch shape of the modal linear step (first use)
+    bool owns_state = true;               // false: u[0], u[1] are the caller's (crkdg_create_on_buffers)
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -348,13 +349,24 @@ __global__ void set_run_params(DevState* ds, double cfl, double t_end) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-const char* crkdg_last_error(void) { return g_err.c_str(); }
-const char* crkdg_version(void) { return "crkdg-gb300 1.0 (sm_103a)"; }
+// the values of one state copy for these arguments (host arithmetic only)
+size_t state_values(const crkdg_mesh* mesh, int k, int basis, int physics, int precision) {
+    const int dim = mesh->dim;
+    const size_t ncell = (size_t)mesh->nx * (dim == 2 ? mesh->ny : 1);
+    const int nv = physics == CRKDG_ADVECTION ? 1 : (dim == 1 ? 3 : 4);
+    const int nm = n_modes(dim, k, dim == 1 ? CRKDG_BASIS_P : basis);
+    return ncell * nv * nm * (compensated(precision) ? 2 : 1);
+}
 
-int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab, double gamma,
-                 int physics, int precision, const double* phys_params, void* stream, crkdg_ctx** out) {
+}  // namespace
+
+namespace {
+
+int create_impl(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab, double gamma,
+                int physics, int precision, const double* phys_params, void* stream, void* buf_a, void* buf_b,
+                crkdg_ctx** out) {
     if (!mesh || !tab || !out) return fail(CRKDG_EINVAL, "null argument");
     *out = nullptr;
     if (mesh->dim != 1 && mesh->dim != 2) return fail(CRKDG_EINVAL, "dim must be 1 or 2");
@@ -427,10 +439,16 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
         crkdg_destroy(c);
         return code;
     };
-    for (int b = 0; b < 2; ++b) {
-        if (cudaMalloc(&c->u[b], c->elems * c->esize * c->planes) != cudaSuccess)
-            return bail(fail(CRKDG_ENOMEM, "cudaMalloc of the state failed"));
-        cudaMemsetAsync(c->u[b], 0, c->elems * c->esize * c->planes, c->stream);
+    if (buf_a) {   // the caller's copies: kept as they are (the state starts as buf_a's contents)
+        c->owns_state = false;
+        c->u[0] = buf_a;
+        c->u[1] = buf_b;
+    } else {
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMalloc(&c->u[b], c->elems * c->esize * c->planes) != cudaSuccess)
+                return bail(fail(CRKDG_ENOMEM, "cudaMalloc of the state failed"));
+            cudaMemsetAsync(c->u[b], 0, c->elems * c->esize * c->planes, c->stream);
+        }
     }
     unsigned char htab[crk::TAB_BYTES];
     crk::pack_tableau(tab->s, tab->a, tab->b, tab->c, htab);
@@ -454,12 +472,73 @@ int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg
     return CRKDG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+const char* crkdg_last_error(void) { return g_err.c_str(); }
+const char* crkdg_version(void) { return "crkdg-gb300 1.0 (sm_103a)"; }
+
+
+int crkdg_state_bytes(const crkdg_mesh* mesh, int k, int basis, int physics, int precision, size_t* bytes) {
+    if (!mesh || !bytes) return fail(CRKDG_EINVAL, "null argument");
+    if ((mesh->dim != 1 && mesh->dim != 2) || mesh->nx < 1 || (mesh->dim == 2 && mesh->ny < 1) || k < 0 || k > 3 ||
+        (basis != CRKDG_BASIS_P && basis != CRKDG_BASIS_Q) ||
+        (physics != CRKDG_ADVECTION && physics != CRKDG_EULER) ||
+        (precision != CRKDG_F32 && precision != CRKDG_F64 && !compensated(precision)))
+        return fail(CRKDG_EINVAL, "bad mesh, degree, basis, physics or precision");
+    *bytes = state_values(mesh, k, basis, physics, precision) * (precision == CRKDG_F64 ? 8 : 4);
+    return CRKDG_OK;
+}
+
+int crkdg_create(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab, double gamma,
+                 int physics, int precision, const double* phys_params, void* stream, crkdg_ctx** out) {
+    return create_impl(mesh, k, basis, flux, tab, gamma, physics, precision, phys_params, stream, nullptr, nullptr,
+                       out);
+}
+
+int crkdg_create_on_buffers(const crkdg_mesh* mesh, int k, int basis, int flux, const crkdg_tableau* tab,
+                            double gamma, int physics, int precision, const double* phys_params, void* stream,
+                            void* state_a, void* state_b, crkdg_ctx** out) {
+    if (!out) return fail(CRKDG_EINVAL, "null argument");
+    *out = nullptr;
+    if (!state_a || !state_b) return fail(CRKDG_EINVAL, "null state buffer");
+    size_t bytes = 0;
+    int r = crkdg_state_bytes(mesh, k, basis, physics, precision, &bytes);
+    if (r) return r;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(state_a), b = reinterpret_cast<uintptr_t>(state_b);
+    if (a % 16 != 0 || b % 16 != 0) return fail(CRKDG_EINVAL, "state buffers must be 16-byte aligned");
+    if ((a < b ? b - a : a - b) < bytes) return fail(CRKDG_EINVAL, "state buffers overlap");
+    // both must be device memory of the current device
+    for (void* p : {state_a, state_b}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(CRKDG_EINVAL, "state buffers must be device memory");
+        }
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || at.device != dev)
+            return fail(CRKDG_EINVAL, "state buffers must be on the current device");
+    }
+    return create_impl(mesh, k, basis, flux, tab, gamma, physics, precision, phys_params, stream, state_a, state_b,
+                       out);
+}
+
+int crkdg_current_state(const crkdg_ctx* c, int* which, void** dev_ptr) {
+    if (check_ctx(c)) return CRKDG_EINVAL;
+    if (which) *which = c->cur;
+    if (dev_ptr) *dev_ptr = c->u[c->cur];
+    return CRKDG_OK;
+}
+
+
 void crkdg_destroy(crkdg_ctx* c) {
     if (!c) return;
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    for (int b = 0; b < 2; ++b)
-        if (c->u[b]) cudaFree(c->u[b]);
+    if (c->owns_state)
+        for (int b = 0; b < 2; ++b)
+            if (c->u[b]) cudaFree(c->u[b]);
     if (c->d_tab) cudaFree(c->d_tab);
     if (c->d_state) cudaFree(c->d_state);
     if (c->d_partials) cudaFree(c->d_partials);

@@ -54,6 +54,37 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(B):
     assert b"tableau" in B.lib().crkdg_last_error()
 
 
+def test_state_bytes_and_caller_buffer_checks(B):
+    """crkdg_state_bytes from the layout (cells x variables x modes, 4 or 8
+    bytes, two plane sets for the compensated states), and the checks of
+    crkdg_create_on_buffers that come before any CUDA call."""
+    from paper_2307_06471_gb300 import tableaux as T
+    per = [B.BC_PERIODIC] * 4
+    m2 = B.make_mesh(2, 30, 7, (0, 1, 0, 1), per)
+    m1 = B.make_mesh(1, 50, 1, (0, 1, 0, 1), per)
+    assert B.state_bytes(m2, 2, B.BASIS_P, B.EULER, B.F32) == 30 * 7 * 4 * 6 * 4
+    assert B.state_bytes(m2, 2, B.BASIS_Q, B.EULER, B.F64) == 30 * 7 * 4 * 9 * 8
+    assert B.state_bytes(m2, 3, B.BASIS_P, B.ADVECTION, B.F32) == 30 * 7 * 1 * 10 * 4
+    assert B.state_bytes(m2, 2, B.BASIS_Q, B.EULER, B.F32D) == 30 * 7 * 4 * 9 * 4 * 2
+    assert B.state_bytes(m1, 2, B.BASIS_Q, B.EULER, B.F64) == 50 * 3 * 3 * 8   # 1D: P^k, 3 variables
+    n = C.c_size_t()
+    assert B.lib().crkdg_state_bytes(C.byref(m2), 4, B.BASIS_P, B.EULER, B.F32, C.byref(n)) == B.EINVAL
+    assert B.lib().crkdg_state_bytes(C.byref(m2), 2, B.BASIS_P, B.EULER, 9, C.byref(n)) == B.EINVAL
+    t = B.make_tableau(*T.SSPRK3)
+    pp = (C.c_double * 2)(1.0, 0.0)
+    out = C.c_void_p()
+    nb = B.state_bytes(m2, 2, B.BASIS_P, B.EULER, B.F32)
+
+    def make(a, b):
+        return B.lib().crkdg_create_on_buffers(C.byref(m2), 2, B.BASIS_P, B.FLUX_LLF, C.byref(t), 1.4, B.EULER,
+                                               B.F32, pp, None, C.c_void_p(a), C.c_void_p(b), C.byref(out))
+    base = 1 << 40   # never dereferenced: every case fails a check first
+    assert make(0, base) == B.EINVAL                      # null
+    assert make(base + 4, base + 2 * nb) == B.EINVAL      # misaligned
+    assert make(base, base + nb - 16) == B.EINVAL         # overlapping
+    assert out.value is None
+
+
 def test_batch_create_rejects_bad_arguments(B):
     from paper_2307_06471_gb300 import tableaux as T
     arr = (B.BatchProblem * 1)(B.BatchProblem(8, 8, 0.0, 1.0, 0.0, 1.0))
