@@ -444,11 +444,16 @@ constexpr size_t mlp_smem_bytes(int nthr) {
 // neighbouring cell move to its base by the deviation of the base
 // difference.  Inner stages, final stage and the update all run on the FP32
 // pipe.
+// SQ = true (square cells, dx == dy, so 1/dx == 1/dy): the volume and face
+// terms accumulate without the 1/dx factors, applied once to each local
+// operator value and to the update (rx (sx + sy - V) for rx sx + ry sy - V):
+// 8 multiplications per volume point and 4 packed ones per face point fewer.
 template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false,
-          class PV>
+          bool SQ = false, class PV>
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
     static_assert(!DEV || (COMP && PHYS == PHYS_EULER && sizeof(T) == 4 && !MLPI && !LIM && !CRK_LF_REUSE),
                   "the deviation form is built for the compensated FP32 2D Euler step without limiters");
+    static_assert(!SQ || (!COMP && !DEV && !CRK_LF_REUSE), "the square-cell form is built for the plain state");
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
     constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
@@ -515,6 +520,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         ph.by = T(a.beta[1]);
     }
     const T rx = opaque(pv.rxT()), ry = opaque(pv.ryT());   // held in registers, as when computed
+    // the factors of the volume and face terms (SQ: 1, applied later)
+    const T rxv = SQ ? T(1) : rx, ryv = SQ ? T(1) : ry;
     const T tdt = T(dt);
     const T Mdx2 = pv.Mdx2T(), Mdy2 = pv.Mdy2T();
     const T gam = T(a.gamma);
@@ -767,7 +774,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 if constexpr (NV % 2 == 0) {
 #pragma unroll
                     for (int v = 0; v < NV; v += 2) {
-                        const T gx0 = rx * fx[v], gx1 = rx * fx[v + 1], gy0 = ry * fy[v], gy1 = ry * fy[v + 1];
+                        const T gx0 = rxv * fx[v], gx1 = rxv * fx[v + 1], gy0 = ryv * fy[v], gy1 = ryv * fy[v + 1];
 #pragma unroll
                         for (int m = 0; m < NM; ++m) {
                             if (tb.gx[q][m] != 0.0) pfma(vol[v][m], vol[v + 1][m], gx0, gx1, T(tb.gx[q][m]));
@@ -777,7 +784,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 } else {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const T gxv = rx * fx[v], gyv = ry * fy[v];
+                        const T gxv = rxv * fx[v], gyv = ryv * fy[v];
 #pragma unroll
                         for (int m = 0; m < NM; ++m) {
                             if (tb.gx[q][m] != 0.0) vol[v][m] += gxv * T(tb.gx[q][m]);
@@ -901,10 +908,12 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                             padd(xp0, xp1, fe[v], fe[v + 1], fw[v], fw[v + 1]);
                             psub(ym0, ym1, fn[v], fn[v + 1], fs[v], fs[v + 1]);
                             padd(yp0, yp1, fn[v], fn[v + 1], fs[v], fs[v + 1]);
-                            pmul(xm0, xm1, rx);
-                            pmul(xp0, xp1, rx);
-                            pmul(ym0, ym1, ry);
-                            pmul(yp0, yp1, ry);
+                            if constexpr (!SQ) {
+                                pmul(xm0, xm1, rx);
+                                pmul(xp0, xp1, rx);
+                                pmul(ym0, ym1, ry);
+                                pmul(yp0, yp1, ry);
+                            }
 #pragma unroll
                             for (int m = 0; m < NM; ++m) {
                                 if (tb.pE[p][m] != 0.0) {
@@ -922,15 +931,16 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         for (int v = 0; v < NV; ++v)
 #pragma unroll
                             for (int m = 0; m < NM; ++m)
-                                floc[v][m] += rx * (fe[v] * T(tb.pE[p][m]) - fw[v] * T(tb.pW[p][m])) +
-                                              ry * (fn[v] * T(tb.pN[p][m]) - fs[v] * T(tb.pS[p][m]));
+                                floc[v][m] += rxv * (fe[v] * T(tb.pE[p][m]) - fw[v] * T(tb.pW[p][m])) +
+                                              ryv * (fn[v] * T(tb.pN[p][m]) - fs[v] * T(tb.pS[p][m]));
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
                     for (int m = 0; m < NM; ++m)
-                        slot(i * C::NDOF + v * NM + m) = T(tb.cm[m]) * (floc[v][m] - vol[v][m]);
+                        slot(i * C::NDOF + v * NM + m) =
+                            T(tb.cm[m]) * (SQ ? rx * (floc[v][m] - vol[v][m]) : floc[v][m] - vol[v][m]);
             }
             if (!need_flux) continue;
             // east face: own east trace vs. the west trace of the lane to the right
@@ -1209,7 +1219,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
                     sy -= FS[p][v] * T(tb.pS[p][m]);
                 }
-                P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * (rx * sx + ry * sy - V(v, m));
+                const T fsum = SQ ? rx * (sx + sy - V(v, m)) : rx * sx + ry * sy - V(v, m);
+                P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * fsum;
             }
         if (r == ny - 1 && !pery) {
             // top boundary: north face flux from the stored north traces
@@ -1269,7 +1280,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 
 // One problem: the launch arguments describe the mesh; dt and t come from
 // the arguments or from the device run state (device-driven runs).
-template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false>
+template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false,
+          bool SQ = false>
 __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MINB_ADV : CRK_STEP_MINB2)
     step2d_kernel(const StepArgs a) {
     if constexpr (MLPI) {
@@ -1282,7 +1294,7 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MIN
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= a.n_strips * a.n_segs) return;   // whole warp leaves; no block barriers
     const ArgsView<T> pv{a, a.dt_from_dev ? a.ds->t : a.t, a.dt_from_dev ? a.ds->dt : a.dt};
-    step2d_body<T, K, B, PHYS, COMP, MLPI, LIM, DEV>(a, pv, gw);
+    step2d_body<T, K, B, PHYS, COMP, MLPI, LIM, DEV, SQ>(a, pv, gw);
 }
 
 // Batched ensemble: problems of different sizes and domains share the
