@@ -256,6 +256,7 @@ int crkdg_batch_create(const crkdg_batch_problem* probs, int n, const int* bc, i
         pb.dy = (q.y1 - q.y0) / q.ny;
         pb.rx = 1.0 / pb.dx;
         pb.ry = 1.0 / pb.dy;
+        pb.sq = pb.dx == pb.dy ? 1 : 0;
         b->probs.push_back(pb);
         off += (size_t)q.nx * q.ny * b->nv * b->nm;
     }

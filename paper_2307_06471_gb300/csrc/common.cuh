@@ -93,6 +93,7 @@ struct BatchProblem {
     double rx, ry;         // 1/dx, 1/dy (host)
     int n_strips, n_segs;
     int warp0;             // first task / reduction slot of the problem
+    int sq;                // 1: square cells (dx == dy), the square-cell form of the step
 };
 
 // -------------------------------------------------------------------------

@@ -9,10 +9,10 @@
 namespace crk {
 namespace {
 
-template <int K, int B>
-cudaError_t run_step_d(const StepArgs& a, int wpb, cudaStream_t st) {
+template <int K, int B, bool SQ>
+cudaError_t run_step_dt(const StepArgs& a, int wpb, cudaStream_t st) {
     using C = Step2D<float, K, B, PHYS_EULER>;
-    auto kern = step2d_kernel<float, K, B, PHYS_EULER, true, false, false, true>;
+    auto kern = step2d_kernel<float, K, B, PHYS_EULER, true, false, false, true, SQ>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -28,6 +28,16 @@ cudaError_t run_step_d(const StepArgs& a, int wpb, cudaStream_t st) {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_finalize<4>(b, st);
+}
+
+// square cells (dx == dy) take the square-cell form for k = 2
+template <int K, int B>
+cudaError_t run_step_d(const StepArgs& a, int wpb, cudaStream_t st) {
+#ifndef CRK_SQ_STEP_OFF
+    if constexpr (K == 2)
+        if (a.dx == a.dy) return run_step_dt<K, B, true>(a, wpb, st);
+#endif
+    return run_step_dt<K, B, false>(a, wpb, st);
 }
 
 template <int K, int B>

@@ -68,8 +68,9 @@ cudaError_t info2d_euler_f32d(int k, int basis, int s, KernelInfo* info);
 // FP32 2D Euler k = 2 step with the fused learned indicator, and the
 // limiter pass that evaluates the indicator
 cudaError_t step2d_euler_f32_mlp(int k, int basis, const StepArgs& a, int wpb, cudaStream_t st);
-// FP32 2D Euler, k = 2, square cells (dx == dy), no limit on load
-cudaError_t step2d_euler_f32_sq(int basis, const StepArgs& a, int wpb, cudaStream_t st);
+// 2D Euler, k = 2, square cells (dx == dy), no limit on load, FP32 / FP64
+cudaError_t step2d_sq_euler_f32(int basis, const StepArgs& a, int wpb, cudaStream_t st);
+cudaError_t step2d_sq_euler_f64(int basis, const StepArgs& a, int wpb, cudaStream_t st);
 cudaError_t limit2d_euler_f32_mlp(int k, int basis, const StepArgs& a, void* u, unsigned long long* flags,
                                   cudaStream_t st);
 // the pass with the network on the tcgen05 tensor cores

@@ -453,7 +453,7 @@ template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false,
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
     static_assert(!DEV || (COMP && PHYS == PHYS_EULER && sizeof(T) == 4 && !MLPI && !LIM && !CRK_LF_REUSE),
                   "the deviation form is built for the compensated FP32 2D Euler step without limiters");
-    static_assert(!SQ || (!COMP && !DEV && !CRK_LF_REUSE), "the square-cell form is built for the plain state");
+    static_assert(!SQ || !CRK_LF_REUSE, "the square-cell form is built without the reused face fluxes");
     using C = Step2D<T, K, B, PHYS>;
     using TBL = typename C::TB;
     constexpr int NQ = C::NQ, NQV = C::NQV, NM = C::NM, NV = C::NV;
@@ -1302,8 +1302,10 @@ __global__ void __launch_bounds__(CRK_STEP_MAXT, PHYS == PHYS_ADV ? CRK_STEP_MIN
 // (t, dt from its own FP64 wave-speed reduction, t_end, status) and buffer
 // index.  Warps take (problem, warp) tasks from a flattened table.  A problem
 // whose dt is 0 (it reached t_end) costs nothing: its warps return at once.
+// SQ: problems with square cells (pb.sq) take the square-cell form of the
+// step (a branch per task, uniform over the warp), the others the general one.
 
-template <class T, int K, int B, int PHYS, bool LIM = true>
+template <class T, int K, int B, int PHYS, bool LIM = true, bool SQ = false>
 __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, const BatchProblem* __restrict__ probs,
                                                            const int2* __restrict__ tasks, int n_tasks,
                                                            DevState* states, int* curs, unsigned* done,
@@ -1340,7 +1342,13 @@ __global__ void __launch_bounds__(256) batch_step2d_kernel(const StepArgs a, con
     pv.ds_ = ds;
     pv.cur_ = curs + tk.x;
     pv.done_ = done;
-    step2d_body<T, K, B, PHYS, false, false, LIM>(a, pv, tk.y);
+    if constexpr (SQ) {
+        if (pb.sq) {
+            step2d_body<T, K, B, PHYS, false, false, LIM, false, true>(a, pv, tk.y);
+            return;
+        }
+    }
+    step2d_body<T, K, B, PHYS, false, false, LIM, false, false>(a, pv, tk.y);
 }
 
 }  // namespace crk
