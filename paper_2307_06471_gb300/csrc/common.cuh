@@ -123,8 +123,9 @@ template <class T> struct Phys<T, PHYS_EULER> {
         const T w = u[1] * ir, v = u[2] * ir;
         const T p = gm1 * (u[3] - T(0.5) * (u[1] * w + u[2] * v));
         const T ep = u[3] + p;
-        fx[0] = u[1]; fx[1] = u[1] * w + p; fx[2] = u[2] * w; fx[3] = w * ep;
-        fy[0] = u[2]; fy[1] = u[1] * v; fy[2] = u[2] * v + p; fy[3] = v * ep;
+        const T muv = u[1] * v;   // rho u v, the x flux of rho v and the y flux of rho u
+        fx[0] = u[1]; fx[1] = u[1] * w + p; fx[2] = muv; fx[3] = w * ep;
+        fy[0] = u[2]; fy[1] = muv; fy[2] = u[2] * v + p; fy[3] = v * ep;
     }
     // normal flux and wave speed |v_n| + c
     template <int AXIS>
@@ -252,7 +253,8 @@ struct EulerDev {
 // Lax--Friedrichs flux through a face with normal +e_AXIS from the state on
 // the low side uL to the state on the high side uR; alpha is local to the
 // point: max of |f'.nu| over both traces.
-template <class T, int PHYS, int AXIS>
+// HALF = false: twice the flux (the factor 1/2 left to the caller's weights)
+template <class T, int PHYS, int AXIS, bool HALF = true>
 __device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const T* uR, T* F) {
     constexpr int NV = Phys<T, PHYS>::NV;
     T fL[NV], fR[NV];
@@ -260,29 +262,29 @@ __device__ __forceinline__ void llf(const Phys<T, PHYS>& ph, const T* uL, const 
     const T sR = ph.template fluxn<AXIS>(uR, fR);
     const T al = sL > sR ? sL : sR;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+    for (int v = 0; v < NV; ++v) F[v] = (HALF ? T(0.5) : T(1)) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
 }
 
 // The same flux in deviation form: uL, uR and F are deviations from the
 // base of ph (F = fhat - f(c).nu; the jump uR - uL is the same).
-template <class T, int AXIS>
+template <class T, int AXIS, bool HALF = true>
 __device__ __forceinline__ void llf(const EulerDev<T>& ph, const T* uL, const T* uR, T* F) {
     T fL[4], fR[4];
     const T sL = ph.template fluxn<AXIS>(uL, fL);
     const T sR = ph.template fluxn<AXIS>(uR, fR);
     const T al = sL > sR ? sL : sR;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) F[v] = T(0.5) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
+    for (int v = 0; v < 4; ++v) F[v] = (HALF ? T(0.5) : T(1)) * ((fL[v] + fR[v]) - al * (uR[v] - uL[v]));
 }
 
 // llf for either kind of flux object (physical fluxes or deviation form)
-template <int AXIS, class T, int PHYS>
+template <int AXIS, bool HALF = true, class T, int PHYS>
 __device__ __forceinline__ void llf_ax(const Phys<T, PHYS>& ph, const T* uL, const T* uR, T* F) {
-    llf<T, PHYS, AXIS>(ph, uL, uR, F);
+    llf<T, PHYS, AXIS, HALF>(ph, uL, uR, F);
 }
-template <int AXIS, class T>
+template <int AXIS, bool HALF = true, class T>
 __device__ __forceinline__ void llf_ax(const EulerDev<T>& ph, const T* uL, const T* uR, T* F) {
-    llf<T, AXIS>(ph, uL, uR, F);
+    llf<T, AXIS, HALF>(ph, uL, uR, F);
 }
 
 // The Lax--Friedrichs flux of llf from states whose normal fluxes and wave

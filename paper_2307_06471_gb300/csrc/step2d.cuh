@@ -713,6 +713,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 
         for (int i = 0; i < S; ++i) {
             const T bi = tab_bT<T>(a, i);
+            const T hbi = T(0.5) * bi;   // the weight of the east and south fluxes formed without their 1/2
             const bool need_L = i < S - 1;
             const bool need_flux = bi != T(0);
             if (!need_L && !need_flux) continue;
@@ -1020,9 +1021,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T F[NV];
-                    llf_ax<0>(ph, tE[p], tWn[p], F);
+                    llf_ax<0, false>(ph, tE[p], tWn[p], F);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) FE[p][v] += bi * F[v];
+                    for (int v = 0; v < NV; ++v) FE[p][v] += hbi * F[v];
                 }
             }
             // south face: north trace of the row below (stored) vs. own south trace
@@ -1050,9 +1051,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
                     T F[NV];
-                    llf_ax<1>(ph, lo[p], tS[p], F);
+                    llf_ax<1, false>(ph, lo[p], tS[p], F);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) FS[p][v] += bi * F[v];
+                    for (int v = 0; v < NV; ++v) FS[p][v] += hbi * F[v];
                 }
             }
             if (keep_north) {
