@@ -468,7 +468,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
     const int offP = offN + S * NQ * NV;
     const int offV = offP + C::NDOF;
     const int offNF = offV + (CRK_V_SMEM ? C::NDOF : 0);   // north fluxes + speeds (CRK_LF_REUSE)
-    auto slot = [&](int k) -> T& { return sm[k * nthr + tid]; };
+    // the thread's private slots: its warp holds smem_per_thread(S) rows of
+    // 32 values, one column per lane (consecutive lanes in consecutive banks),
+    // so that slot k sits k * 32 values past the thread's own base
+    T* const smt = sm + (size_t)(tid >> 5) * (C::smem_per_thread(S) * 32) + (tid & 31);
+    auto slot = [&](int k) -> T& { return smt[k * 32]; };
 
     const int lane = tid & 31;
     const int total_warps = pv.total_warps();
