@@ -243,20 +243,34 @@ __device__ __forceinline__ bool limit2d_cell(const StepArgs& a, const LimMesh& g
     const int xe = x < nx - 1 ? x + 1 : (perx ? 0 : nx - 1);
     const bool needW = inside && (lane == 0 || x == 0), needE = inside && (lane == 31 || x == nx - 1);
     T c[NV][NM], own[NV], nbW[NV], nbE[NV], nbS[NV], nbN[NV];
+    // each address one plane (or one variable's NM planes) past the last:
+    // a running pointer per row instead of an index formed per load
+    const T* pc = u + ((size_t)y * nx + xc);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int m = 0; m < NM; ++m) c[v][m] = u[(size_t)(v * NM + m) * plane + (size_t)y * nx + xc];
+        for (int m = 0; m < NM; ++m) {
+            c[v][m] = *pc;
+            pc += plane;
+        }
+    const T* ps = u + ((size_t)ys * nx + xc);
+    const T* pn = u + ((size_t)yn * nx + xc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        nbS[v] = u[(size_t)(v * NM) * plane + (size_t)ys * nx + xc];
-        nbN[v] = u[(size_t)(v * NM) * plane + (size_t)yn * nx + xc];
+        nbS[v] = *ps;
+        nbN[v] = *pn;
+        ps += NM * plane;
+        pn += NM * plane;
     }
     T ldW[NV], ldE[NV];
+    const T* pw = u + ((size_t)y * nx + xw);
+    const T* pe = u + ((size_t)y * nx + xe);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        ldW[v] = needW ? u[(size_t)(v * NM) * plane + (size_t)y * nx + xw] : T(0);
-        ldE[v] = needE ? u[(size_t)(v * NM) * plane + (size_t)y * nx + xe] : T(0);
+        ldW[v] = needW ? *pw : T(0);
+        ldE[v] = needE ? *pe : T(0);
+        pw += NM * plane;
+        pe += NM * plane;
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
