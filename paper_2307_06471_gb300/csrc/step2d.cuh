@@ -524,7 +524,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
         ph.by = T(a.beta[1]);
     }
     const T rx = opaque(pv.rxT()), ry = opaque(pv.ryT());   // held in registers, as when computed
-    // the factors of the volume and face terms (SQ: 1, applied later)
+    // the factors of the face terms (SQ: 1, applied later); the volume
+    // term keeps its factors, whose products also form the register pairs of
+    // its packed accumulation
     const T rxv = SQ ? T(1) : rx, ryv = SQ ? T(1) : ry;
     const T tdt = T(dt);
     const T Mdx2 = pv.Mdx2T(), Mdy2 = pv.Mdy2T();
@@ -779,7 +781,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 if constexpr (NV % 2 == 0) {
 #pragma unroll
                     for (int v = 0; v < NV; v += 2) {
-                        const T gx0 = rxv * fx[v], gx1 = rxv * fx[v + 1], gy0 = ryv * fy[v], gy1 = ryv * fy[v + 1];
+                        const T gx0 = rx * fx[v], gx1 = rx * fx[v + 1], gy0 = ry * fy[v], gy1 = ry * fy[v + 1];
 #pragma unroll
                         for (int m = 0; m < NM; ++m) {
                             if (tb.gx[q][m] != 0.0) pfma(vol[v][m], vol[v + 1][m], gx0, gx1, T(tb.gx[q][m]));
@@ -789,7 +791,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 } else {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const T gxv = rxv * fx[v], gyv = ryv * fy[v];
+                        const T gxv = rx * fx[v], gyv = ry * fy[v];
 #pragma unroll
                         for (int m = 0; m < NM; ++m) {
                             if (tb.gx[q][m] != 0.0) vol[v][m] += gxv * T(tb.gx[q][m]);
@@ -945,7 +947,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                     for (int m = 0; m < NM; ++m)
                         slot(i * C::NDOF + v * NM + m) =
-                            T(tb.cm[m]) * (SQ ? rx * (floc[v][m] - vol[v][m]) : floc[v][m] - vol[v][m]);
+                            T(tb.cm[m]) * (SQ ? fma(rx, floc[v][m], -vol[v][m]) : floc[v][m] - vol[v][m]);
             }
             if (!need_flux) continue;
             // east face: own east trace vs. the west trace of the lane to the right
@@ -1224,7 +1226,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
                     sy -= FS[p][v] * T(tb.pS[p][m]);
                 }
-                const T fsum = SQ ? rx * (sx + sy - V(v, m)) : rx * sx + ry * sy - V(v, m);
+                const T fsum = SQ ? fma(rx, sx + sy, -V(v, m)) : rx * sx + ry * sy - V(v, m);
                 P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * fsum;
             }
         if (r == ny - 1 && !pery) {
