@@ -444,10 +444,10 @@ constexpr size_t mlp_smem_bytes(int nthr) {
 // neighbouring cell move to its base by the deviation of the base
 // difference.  Inner stages, final stage and the update all run on the FP32
 // pipe.
-// SQ = true (square cells, dx == dy, so 1/dx == 1/dy): the volume and face
-// terms accumulate without the 1/dx factors, applied once to each local
-// operator value and to the update (rx (sx + sy - V) for rx sx + ry sy - V):
-// 8 multiplications per volume point and 4 packed ones per face point fewer.
+// SQ = true (square cells, dx == dy, so 1/dx == 1/dy): the face terms
+// accumulate without the 1/dx factors, applied once to each local-operator
+// value and to the update (rx (sx + sy) - V for rx sx + ry sy - V): 4 packed
+// multiplications per face point fewer.
 template <class T, int K, int B, int PHYS, bool COMP = false, bool MLPI = false, bool LIM = true, bool DEV = false,
           bool SQ = false, class PV>
 __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, const int gw) {
