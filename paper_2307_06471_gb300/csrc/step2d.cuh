@@ -753,29 +753,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
             for (int v = 0; v < NV; ++v)
 #pragma unroll
                 for (int m = 0; m < NM; ++m) vol[v][m] = T(0);
-#pragma unroll
-            for (int q = 0; q < NQV; ++q) {
-                T uq[NV];
-                if constexpr (NV % 2 == 0) {
-#pragma unroll
-                    for (int v = 0; v < NV; v += 2) {
-                        T s0 = T(0), s1 = T(0);
-#pragma unroll
-                        for (int m = 0; m < NM; ++m)   // (P_1 vanishes at the middle Gauss point)
-                            if (tb.phi[q][m] != 0.0) pfma(s0, s1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
-                        uq[v] = s0;
-                        uq[v + 1] = s1;
-                    }
-                } else {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        T s = T(0);
-#pragma unroll
-                        for (int m = 0; m < NM; ++m)
-                            if (tb.phi[q][m] != 0.0) s += w[v][m] * T(tb.phi[q][m]);
-                        uq[v] = s;
-                    }
-                }
+            // flux and projection of the point values uq at volume point q
+            auto vol_point = [&](const int q, const T (&uq)[NV]) {
                 T fx[NV], fy[NV];
                 ph.flux2(uq, fx, fy);
                 if constexpr (NV % 2 == 0) {
@@ -799,6 +778,45 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         }
                     }
                 }
+            };
+            // point values in mirrored pairs: phi_m(-xi, eta) = (-1)^i phi_m(xi,
+            // eta), so the values at xi_a and at -xi_a are the sum and the
+            // difference of the even-i and odd-i parts of one contraction (the
+            // middle column xi = 0 has no odd part)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) {
+                const int qa = q / NQ, qb = q % NQ, qm = (NQ - 1 - qa) * NQ + qb;
+                if (qa > NQ - 1 - qa) continue;   // evaluated with its mirror point
+                T uq[NV], uqm[NV];
+                if constexpr (NV % 2 == 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; v += 2) {
+                        T e0 = T(0), e1 = T(0), o0 = T(0), o1 = T(0);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m)   // (P_1 vanishes at the middle Gauss point)
+                            if (tb.phi[q][m] != 0.0) {
+                                if (tb.ip[m] == 0) pfma(e0, e1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
+                                else pfma(o0, o1, w[v][m], w[v + 1][m], T(tb.phi[q][m]));
+                            }
+                        padd(uq[v], uq[v + 1], e0, e1, o0, o1);
+                        psub(uqm[v], uqm[v + 1], e0, e1, o0, o1);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        T e = T(0), o = T(0);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m)
+                            if (tb.phi[q][m] != 0.0) {
+                                if (tb.ip[m] == 0) e += w[v][m] * T(tb.phi[q][m]);
+                                else o += w[v][m] * T(tb.phi[q][m]);
+                            }
+                        uq[v] = e + o;
+                        uqm[v] = e - o;
+                    }
+                }
+                vol_point(q, uq);
+                if (qa < NQ - 1 - qa) vol_point(qm, uqm);
             }
             if (need_flux && out_row) {
                 if constexpr (NV % 2 == 0) {
