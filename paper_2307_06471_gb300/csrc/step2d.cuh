@@ -779,6 +779,51 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                     }
                 }
             };
+            // a mirrored pair of points (q at xi, its mirror at -xi): w_q dphi/dxi
+            // changes sign with (-1)^(i-1) and w_q dphi/deta with (-1)^i, so
+            // each mode takes the sum or the difference of the two points'
+            // fluxes: one product per mode and direction for both points
+            auto vol_pair = [&](const int q, const T (&uq)[NV], const T (&uqm)[NV]) {
+                T fx[NV], fy[NV], hx[NV], hy[NV];
+                ph.flux2(uq, fx, fy);
+                ph.flux2(uqm, hx, hy);
+                if constexpr (NV % 2 == 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; v += 2) {
+                        T sx0, sx1, dx0, dx1, sy0, sy1, dy0, dy1;
+                        padd(sx0, sx1, fx[v], fx[v + 1], hx[v], hx[v + 1]);
+                        psub(dx0, dx1, fx[v], fx[v + 1], hx[v], hx[v + 1]);
+                        padd(sy0, sy1, fy[v], fy[v + 1], hy[v], hy[v + 1]);
+                        psub(dy0, dy1, fy[v], fy[v + 1], hy[v], hy[v + 1]);
+                        pmul(sx0, sx1, rx);
+                        pmul(dx0, dx1, rx);
+                        pmul(sy0, sy1, ry);
+                        pmul(dy0, dy1, ry);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            if (tb.gx[q][m] != 0.0) {
+                                if (tb.ip[m] == 0) pfma(vol[v][m], vol[v + 1][m], dx0, dx1, T(tb.gx[q][m]));
+                                else pfma(vol[v][m], vol[v + 1][m], sx0, sx1, T(tb.gx[q][m]));
+                            }
+                            if (tb.gy[q][m] != 0.0) {
+                                if (tb.ip[m] == 0) pfma(vol[v][m], vol[v + 1][m], sy0, sy1, T(tb.gy[q][m]));
+                                else pfma(vol[v][m], vol[v + 1][m], dy0, dy1, T(tb.gy[q][m]));
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const T sxv = rx * (fx[v] + hx[v]), dxv = rx * (fx[v] - hx[v]);
+                        const T syv = ry * (fy[v] + hy[v]), dyv = ry * (fy[v] - hy[v]);
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            if (tb.gx[q][m] != 0.0) vol[v][m] += (tb.ip[m] == 0 ? dxv : sxv) * T(tb.gx[q][m]);
+                            if (tb.gy[q][m] != 0.0) vol[v][m] += (tb.ip[m] == 0 ? syv : dyv) * T(tb.gy[q][m]);
+                        }
+                    }
+                }
+            };
             // point values in mirrored pairs: phi_m(-xi, eta) = (-1)^i phi_m(xi,
             // eta), so the values at xi_a and at -xi_a are the sum and the
             // difference of the even-i and odd-i parts of one contraction (the
@@ -815,8 +860,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                         uqm[v] = e - o;
                     }
                 }
-                vol_point(q, uq);
-                if (qa < NQ - 1 - qa) vol_point(qm, uqm);
+                if (qa < NQ - 1 - qa) vol_pair(q, uq, uqm);
+                else vol_point(q, uq);
             }
             if (need_flux && out_row) {
                 if constexpr (NV % 2 == 0) {
