@@ -1250,7 +1250,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 for (int m = 0; m < NM; ++m) {
                     T s = T(0);
 #pragma unroll
-                    for (int p = 0; p < NQ; ++p) s += FS[p][v] * T(tb.pN[p][m]);
+                    for (int p = 0; p < NQ; ++p)
+                        if (tb.pN[p][m] != 0.0) s += FS[p][v] * T(tb.pN[p][m]);
                     if constexpr (DEV) {
                         if (tb.sN[m] != 0.0) s -= gS[v] * T(tb.sN[m]);
                     }
@@ -1278,6 +1279,15 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
 #pragma unroll
                 for (int v = 0; v < NV; ++v) FW[p][v] += gW[v];
         }
+        // east and west faces: pW = (-1)^i pE, so FE pE - FW pW = pE (FE -+ FW)
+        T FEm[NQ][NV], FEp[NQ][NV];
+#pragma unroll
+        for (int p = 0; p < NQ; ++p)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                FEm[p][v] = FE[p][v] - FW[p][v];
+                FEp[p][v] = FE[p][v] + FW[p][v];
+            }
         T P[NV][NM];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
@@ -1286,8 +1296,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs& a, const PV& pv, con
                 T sx = T(0), sy = T(0);
 #pragma unroll
                 for (int p = 0; p < NQ; ++p) {
-                    sx += FE[p][v] * T(tb.pE[p][m]) - FW[p][v] * T(tb.pW[p][m]);
-                    sy -= FS[p][v] * T(tb.pS[p][m]);
+                    if (tb.pE[p][m] != 0.0) sx += (tb.ip[m] == 0 ? FEm[p][v] : FEp[p][v]) * T(tb.pE[p][m]);
+                    if (tb.pS[p][m] != 0.0) sy -= FS[p][v] * T(tb.pS[p][m]);
                 }
                 const T fsum = SQ ? fma(rx, sx + sy, -V(v, m)) : rx * sx + ry * sy - V(v, m);
                 P[v][m] = (COMP ? T(0) : un[v][m]) - tdt * T(tb.cm[m]) * fsum;
