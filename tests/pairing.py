@@ -170,3 +170,63 @@ def tvb_margin(dg, u, t, M, cells):
                     sc = max(scale[0][f], scale[1][f], scale[2][f], 1e-300)
                     best = min(best, abs(abs(a[0][f]) - other) / sc)
     return best
+
+
+def positivity_root_tie(dg, lim_cell, got_cell, eps, e32=2.0 ** -24):
+    """Whether an FP32 result `got_cell` [v, m] of the positivity scaling that
+    misses the value band against the oracle is the oracle's scaling with its
+    pressure factor taken within FP32 rounding of a near-double root.
+
+    The scaling (Zhang and Shu, applied after the TVB limiter; `lim_cell` is
+    its input) multiplies the density's non-constant modes by theta1 and then
+    every non-constant mode by theta2, the smallest root in (0, 1] of
+    a t^2 + b t + c over the points where the pressure at t = 1 is below eps.
+    A root r = (-b -+ sqrt(D)) / 2a moves by dD / (4 |a| sqrt(D)) when the
+    discriminant D = b^2 - 4ac moves by dD; FP32 rounding of b^2 and 4ac
+    gives dD of a few e32 (b^2 + 4|ac|), so the root moves by about
+    e32 (b^2 + 4|ac|) / D * |r2 - r1| / 4, large where the roots nearly
+    coincide (D small against b^2).  theta1 is a well-conditioned quotient.
+
+    Accepted when: the cell average is unchanged; the non-constant modes are
+    those of `lim_cell` times theta2' (and the oracle's theta1 for the
+    density) to FP32 rounding; and |theta2' - theta2| is within 4 e32
+    (b^2 + 4|ac|) / D |r2 - r1| + 1e-6 at the point that binds theta2."""
+    from oracle.limiter import positivity_points
+    P = positivity_points(dg)
+    lim = np.asarray(lim_cell, dtype=np.float64)
+    got = np.asarray(got_cell, dtype=np.float64)
+    g = dg.phys.gamma
+    if not np.array_equal(got[:, 0], lim[:, 0]):
+        return False
+    # theta1 and the points' quadratics, in FP64
+    rho = P @ lim[0]
+    rb = lim[0, 0]
+    th1 = min(1.0, (rb - eps) / (rb - rho.min())) if rho.min() < eps else 1.0
+    u = lim.copy()
+    u[0, 1:] *= th1
+    d = (u @ P.T) - u[:, :1]
+    ub = u[:, 0]
+    k = eps / (g - 1.0)
+    a = d[0] * d[-1] - 0.5 * np.sum(d[1:-1] ** 2, axis=0)
+    b = ub[0] * d[-1] + ub[-1] * d[0] - ub[1:-1] @ d[1:-1] - k * d[0]
+    c = ub[0] * ub[-1] - 0.5 * np.sum(ub[1:-1] ** 2) - k * ub[0]
+    th2, bound = 1.0, 1e-6
+    for q in np.where(a + b + c < 0.0)[0]:
+        D = b[q] * b[q] - 4.0 * a[q] * c
+        sq = np.sqrt(max(D, 0.0))
+        qq = -0.5 * (b[q] + (sq if b[q] >= 0 else -sq))
+        roots = [r for r in ((c / qq) if qq != 0 else np.inf, (qq / a[q]) if a[q] != 0 else np.inf) if 0 < r <= 1]
+        r = min(roots) if roots else 0.0
+        if r < th2:
+            th2 = r
+            spread = sq / abs(a[q]) if a[q] != 0 else 0.0
+            bound = 4.0 * e32 * (b[q] * b[q] + 4.0 * abs(a[q] * c)) / max(D, 1e-300) * spread + 1e-6
+    # theta2' of the result: the momentum and energy modes' common factor
+    sel = [(v, m) for v in range(1, lim.shape[0]) for m in range(1, lim.shape[1])
+           if abs(lim[v, m]) > 1e-3 * np.max(np.abs(lim[v, 1:]))]
+    th2g = float(np.median([got[v, m] / lim[v, m] for v, m in sel]))
+    for v in range(lim.shape[0]):
+        f = th2g * (th1 if v == 0 else 1.0)
+        if np.max(np.abs(got[v, 1:] - f * lim[v, 1:])) > 4e-6 * max(np.max(np.abs(lim[v])), 1e-30):
+            return False
+    return abs(th2g - th2) <= bound
