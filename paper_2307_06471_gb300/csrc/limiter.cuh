@@ -13,6 +13,11 @@
 #pragma once
 #include "common.cuh"
 
+// 1: the two directions' characteristic projections as packed FP32x2 FMAs
+#ifndef CRK_LIM_PACKED
+#define CRK_LIM_PACKED 1
+#endif
+
 namespace crk {
 
 template <class T>
@@ -28,6 +33,20 @@ __device__ __forceinline__ T minmod3(T a, T b, T c) {
 template <class T>
 __device__ __forceinline__ T tvb_minmod(T a1, T a2, T a3, T Mh2) {
     return fabs(a1) <= Mh2 ? a1 : minmod3(a1, a2, a3);
+}
+
+// a0 = fma(x0, y0, a0), a1 = fma(x1, y1, a1): one packed FP32x2 FMA for an
+// FP32 pair (each lane rounds like the scalar FMA)
+template <class T>
+__device__ __forceinline__ void fma_pair(T& a0, T& a1, T x0, T x1, T y0, T y1) {
+    if constexpr (sizeof(T) == 4) {
+        const float2 r = __ffma2_rn(make_float2(x0, x1), make_float2(y0, y1), make_float2(a0, a1));
+        a0 = r.x;
+        a1 = r.y;
+    } else {
+        a0 = fma(x0, y0, a0);
+        a1 = fma(x1, y1, a1);
+    }
 }
 
 // The scalars both directions' eigenvectors share at one state: velocity,
@@ -110,6 +129,34 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
     if (NV == 4) {
         T L[4][4], mxc[4], myc[4];
         const EulerEig<T> eg = euler_eig_scalars<T>(avg, gamma);
+#if CRK_LIM_PACKED
+        // both directions' characteristic values at once, x in the first
+        // lane of each pair and y in the second, each sum in the order of v
+        T Ly[4][4];
+        euler_left_of<T, 0>(eg, L);
+        euler_left_of<T, 1>(eg, Ly);
+        T dE[4], dW[4], dN[4], dS[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            dE[v] = nbE[v] - avg[v];
+            dN[v] = nbN[v] - avg[v];
+            dW[v] = avg[v] - nbW[v];
+            dS[v] = avg[v] - nbS[v];
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            T x1 = 0, y1 = 0, x2 = 0, y2 = 0, x3 = 0, y3 = 0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                fma_pair(x1, y1, L[f][v], Ly[f][v], u[v][1], u[v][2]);
+                fma_pair(x2, y2, L[f][v], Ly[f][v], dE[v], dN[v]);
+                fma_pair(x3, y3, L[f][v], Ly[f][v], dW[v], dS[v]);
+            }
+            mxc[f] = tvb_minmod(x1, x2, x3, Mdx2);
+            myc[f] = tvb_minmod(y1, y2, y3, Mdy2);
+            flag |= (mxc[f] != x1) || (myc[f] != y1);
+        }
+#else
         // x direction: characteristic values and the modified minmod
         euler_left_of<T, 0>(eg, L);
 #pragma unroll
@@ -138,6 +185,7 @@ __device__ __forceinline__ bool tvb_limit_cell(T (&u)[NV][NM], const T* nbW, con
             myc[f] = tvb_minmod(s1, s2, s3, Mdy2);
             flag |= (myc[f] != s1);
         }
+#endif
         if (mode >= 0) flag = mode == 1;
         if (flag) {
             // back to conserved variables only for limited cells
