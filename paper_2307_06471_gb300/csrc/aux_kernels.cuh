@@ -9,7 +9,7 @@
 
 // resident blocks per SM the limiter pass is compiled for (tuning knob)
 #ifndef CRK_LIMIT_MINB
-#define CRK_LIMIT_MINB 6
+#define CRK_LIMIT_MINB 7
 #endif
 
 namespace crk {
@@ -318,10 +318,10 @@ __device__ __forceinline__ LimMesh single_mesh(const StepArgs& a) {
 }
 
 // The limiter pass: 128 threads per block along x, one block row per mesh
-// row.  Counts troubled cells (one atomic per warp that has any).  6 blocks
-// per SM (80 registers): at 8 the kernel spills, and it measured 0.0359 ms
-// per pass on the 1920x480 P^2 state against 0.0370 (8 blocks) and 0.0389 (5
-// blocks).
+// row.  Counts troubled cells (one atomic per warp that has any).  7 blocks
+// per SM (72 registers, a few bytes of spills): on the 1920x480 P^2 state
+// 0.0306 ms per pass against 0.0311 at 6 blocks (80 registers, none); 8
+// blocks spill more and measured slower, 5 slower still.
 template <class T, int K, int B, int PHYS>
 __global__ void __launch_bounds__(128, CRK_LIMIT_MINB) limit2d_kernel(const StepArgs a, T* __restrict__ u,
                                                                       unsigned long long* flag_count) {
